@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the QuadBox tile rasteriser on one GB300 (or N replicas).
+
+Workload: 1M Gaussians, 1920x1080, SH degree 3, clustered synthetic scene
+(64 blobs + 20% background at depth 1-50, 10% anisotropic), QuadBox binning
+versus the 3-sigma AABB binning on the same kernels.
+
+A step is one pass of the rasteriser's hot path over the scene: preprocess
+(projection, SH colour, QuadBox, QPass count), scan + emit, onesweep sort +
+ranges, render; the fwd+bwd step adds the hand-written backward.  `value` is
+the QuadBox forward frame rate summed over ranks; the AABB path, fwd+bwd
+times, per-stage times and tile pairs per frame are reported beside it.
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FPS fwd & fwd+bwd ms @1M Gaussians 1080p, QuadBox vs AABB; tile pairs/frame"
+UNIT = "FPS"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--digit-bits", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--out", default=None, help="also write the JSON line here")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2605_04844_gb300 import _native as N
+    from paper_2605_04844_gb300 import rasterizer as R
+    from paper_2605_04844_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    scene_np, cam = synth.config2(args.n, args.width, args.height)
+    W, H, n = cam["width"], cam["height"], args.n
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in scene_np.items() if isinstance(v, np.ndarray)}
+    sd = {k: v.to(dev) for k, v in pinned.items()}
+    sd["sh_degree"], sd["raw"] = scene_np["sh_degree"], 1
+    scene_s, cam_s = R.scene_struct(sd), R.camera_struct(cam)
+    bg = (0.0, 0.0, 0.0)
+
+    # autotuned sort digit width unless given
+    digit_bits = args.digit_bits
+    tune = None
+    if digit_bits is None:
+        from paper_2605_04844_gb300 import autotune
+        tune = autotune.tune_frame(sd, cam, mode="quadbox")
+        digit_bits = tune["digit_bits"]
+
+    frames, pairs = {}, {}
+    for mode in ("quadbox", "aabb3s"):
+        _, fr = R.forward(sd, cam, mode, bg=bg, digit_bits=digit_bits)
+        pairs[mode] = fr.n_pairs
+        cap = int(fr.n_pairs * 1.1) + 4096
+        frames[mode] = R.Frame(n, W, H, cap)
+        frames[mode].set_tuning(digit_bits=digit_bits)
+    img = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    grads = {k: torch.zeros_like(sd[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    gs = N.QbSceneGrads()
+    gs.means, gs.scales, gs.quats = grads["means"].data_ptr(), grads["scales"].data_ptr(), grads["quats"].data_ptr()
+    gs.opacities, gs.sh = grads["opacities"].data_ptr(), grads["sh"].data_ptr()
+    dL = torch.full((3, H, W), 1.0 / (3 * H * W), dtype=torch.float32, device=dev)
+
+    STAGES = ("preprocess", "emit", "sort", "render", "backward")
+
+    def step(fr, with_bwd, ev):
+        ev[0].record(stream)
+        fr.preprocess(scene_s, cam_s, mode_of[id(fr)])
+        ev[1].record(stream)
+        fr.bin_emit(sync=False)
+        ev[2].record(stream)
+        fr.sort()
+        ev[3].record(stream)
+        fr.render(bg, img)
+        ev[4].record(stream)
+        if with_bwd:
+            for g in grads.values():
+                g.zero_()
+            N.qb_render_bwd(fr.frame, scene_s, cam_s, bg, dL, gs, None)
+            ev[5].record(stream)
+
+    mode_of = {id(frames["quadbox"]): "quadbox", id(frames["aabb3s"]): "aabb3s"}
+
+    def run_phase(mode, with_bwd, steps, warmup):
+        fr = frames[mode]
+        nev = 6 if with_bwd else 5
+        for _ in range(warmup):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(nev)]
+            step(fr, with_bwd, evs)
+        torch.cuda.synchronize()
+        recs = []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(nev)]
+            step(fr, with_bwd, evs)
+            recs.append(evs)
+        torch.cuda.synchronize()
+        fr.check()
+        per_stage = {s: 0.0 for s in STAGES}
+        total = 0.0
+        for evs in recs:
+            for i in range(nev - 1):
+                dt = evs[i].elapsed_time(evs[i + 1])
+                per_stage[STAGES[i]] += dt
+                total += dt
+        return total / steps, {s: v / steps for s, v in per_stage.items()}
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    fwd_ms, fwd_stages = run_phase("quadbox", False, args.steps, args.warmup)
+    fb_ms, fb_stages = run_phase("quadbox", True, args.steps, args.warmup)
+    afwd_ms, afwd_stages = run_phase("aabb3s", False, args.steps, args.warmup)
+    afb_ms, afb_stages = run_phase("aabb3s", True, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.time() - t_wall0
+    clk = clocks.stop()
+    fwd_ms_max = max_over_ranks(fwd_ms)
+
+    # ---- render statistics for the ALU roofline (outside the timed region) ----
+    fr = frames["quadbox"]
+    fr.preprocess(scene_s, cam_s, "quadbox")
+    fr.bin_emit(sync=False)
+    fr.sort()
+    fr.render(bg, img)
+    torch.cuda.synchronize()
+    A = fr.arrays(n_pairs=1)
+    n_eval = int(A["n_eval"].to(torch.int64).sum().item()) if "n_eval" in A else None
+
+    # ---- end to end through the public API with host buffers ----
+    host_img = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+    d2h = host_img.numel() * 4
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k, v in pinned.items():
+            sd[k].copy_(v, non_blocking=True)
+        fr.preprocess(scene_s, cam_s, "quadbox")
+        fr.bin_emit(sync=False)
+        fr.sort()
+        fr.render(bg, img)
+        host_img.copy_(img, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1))
+    fr.check()
+    e2e_ms = max_over_ranks(statistics.mean(e2e_times))
+
+    P = pairs["quadbox"]
+    result = {
+        "metric": METRIC,
+        "value": round(world * 1000.0 / fwd_ms_max, 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(fwd_ms_max, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded 1M-Gaussian clustered scene; stands in for Mip-NeRF 360 / DB / T&T)",
+        "config": {"workload": "1M Gaussians, 1920x1080, SH degree 3, 16x16 tiles, QuadBox binning (clamped to "
+                               "3-sigma) vs 3-sigma AABB on the same kernels",
+                   "n_gaussians": n, "width": W, "height": H, "sh_degree": 3,
+                   "l2": "L2 flushed (258 MB write) between timed steps; scene inputs 236 MB > L2",
+                   "sort_digit_bits": digit_bits, "parallelism": f"replicas x{world}"},
+        "quadbox": {"fwd_fps": round(1000.0 / fwd_ms, 2), "fwd_ms": round(fwd_ms, 4),
+                    "fwd_bwd_ms": round(fb_ms, 4), "pairs_per_frame": P,
+                    "stage_ms": {k: round(v, 4) for k, v in fb_stages.items()}},
+        "aabb3s": {"fwd_fps": round(1000.0 / afwd_ms, 2), "fwd_ms": round(afwd_ms, 4),
+                   "fwd_bwd_ms": round(afb_ms, 4), "pairs_per_frame": pairs["aabb3s"],
+                   "stage_ms": {k: round(v, 4) for k, v in afb_stages.items()}},
+        "speedup_vs_aabb": {"fwd": round(afwd_ms / fwd_ms, 3), "fwd_bwd": round(afb_ms / fb_ms, 3),
+                            "pair_ratio": round(pairs["aabb3s"] / max(P, 1), 3)},
+        "paper_context": "paper: 1.85x FPS over 3DGS, mean over Mip-NeRF 360/DB/T&T on NVIDIA A100 (Table 1)",
+        "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clk,
+        "wall_s_timed": round(wall, 2),
+    }
+    result["roofline"] = roofline(fwd_stages, fb_stages, P, n, W, H, digit_bits, n_eval, clk)
+    passes = -(-(31 + (((W + 15) // 16) * ((H + 15) // 16) - 1).bit_length()) // digit_bits)
+    per_fwd = 1 + 3 + 1 + 2 + passes + 1 + 1
+    result["gpu_launches"] = args.steps * (2 * per_fwd + 2 * (per_fwd + 2)) + args.steps * per_fwd
+    if tune:
+        result["autotune"] = tune
+    return result
+
+
+def roofline(fwd_stages, fb_stages, P, n, W, H, digit_bits, n_eval, clk):
+    """Roofline of the dominant kernel of the forward step (see the design doc for
+    the algorithmic bytes and flops per unit)."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    key_bits = 31 + (tiles - 1).bit_length()
+    passes = -(-key_bits // digit_bits)
+    sort_bytes = P * (8 + passes * 24 + 8) + tiles * 8
+    dom = max(fwd_stages, key=lambda k: fwd_stages[k])
+    out = {}
+    if dom == "render" and n_eval:
+        sm_mhz = clk.get("sm_mhz") or 1440.0
+        peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        flops = n_eval * RENDER_FLOPS_PER_EVAL
+        ach = flops / (fwd_stages["render"] * 1e-3) / 1e12
+        out = {"kernel": "render_kernel", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak_tflops, 3),
+               "unit": "TFLOP/s", "frac": round(ach / peak_tflops, 4), "traffic": None,
+               "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median sampled clock)",
+               "evaluations": n_eval}
+    else:
+        ach = sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9
+        out = {"kernel": "onesweep_kernel (+hist, ranges)", "bound": "hbm", "achieved": round(ach, 1),
+               "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    # secondary: the HBM-bound stages
+    emit_bytes = 12 * P + 44 * n
+    out["hbm_stages"] = {
+        "sort": {"GB/s": round(sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9, 1),
+                 "frac": round(sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9 / hbm, 4), "bytes": sort_bytes},
+        "emit": {"GB/s": round(emit_bytes / (fwd_stages["emit"] * 1e-3) / 1e9, 1),
+                 "frac": round(emit_bytes / (fwd_stages["emit"] * 1e-3) / 1e9 / hbm, 4), "bytes": emit_bytes},
+    }
+    out["dominant_stage"] = dom
+    return out
+
+
+# FP32 operations per evaluated (pixel, Gaussian) entry of render_kernel:
+# dx, dy (2), power (3 mul + 2 fma + 1 neg-mul = 6), compare (1), exp (2:
+# scale + ex2), o*G (1), min (1), compare (1), 1-alpha (1), T*(1-alpha) (1),
+# compare (1), alpha*T (1), 3 colour FMAs (3).
+RENDER_FLOPS_PER_EVAL = 22
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_frame_seconds(scene_np, cam, row_stride=16):
+    """One forward frame of the FP64 oracle: projection, binning and sort
+    in full, compositing on every row_stride-th tile row (scaled up)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    W, H = cam["width"], cam["height"]
+    t0 = time.time()
+    s64 = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in scene_np.items()}
+    proj = O.project(s64, cam)
+    L = O.own_lists(proj, W, H, O.QUADBOX, True)
+    t1 = time.time()
+    ty = (H + 15) // 16
+    rows = list(range(0, ty, row_stride))
+    tx = (W + 15) // 16
+    pxs, pys = [], []
+    for r in rows:
+        ys = np.arange(r * 16, min(H, r * 16 + 16))
+        xs = np.arange(W)
+        yy, xx = np.meshgrid(ys, xs, indexing="ij")
+        pxs.append(xx.ravel())
+        pys.append(yy.ravel())
+    pxs, pys = np.concatenate(pxs), np.concatenate(pys)
+    t2 = time.time()
+    O.render_pixels(W, H, pxs, pys, L["ranges"], L["vals"], proj)
+    t3 = time.time()
+    frac = len(pxs) / (W * H)
+    return (t1 - t0) + (t3 - t2) / frac, len(L["vals"]), len(pxs)
+
+
+def cpu_baseline(scene_np, cam):
+    from oracle import oracle as O
+    O.build()
+    secs, P, npx = oracle_frame_seconds(scene_np, cam)
+    cores = os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return {"value": round(1.0 / secs, 5), "unit": UNIT, "cores": int(omp) if omp else cores, "kind": "oracle",
+            "sample": f"one 1M-Gaussian 1920x1080 QuadBox frame: FP64 projection, binning and sort in full, "
+                      f"compositing of every 16th tile row ({npx} pixels) scaled to the frame",
+            "seconds_per_frame": round(secs, 3)}
+
+
+def run_reference(args):
+    from paper_2605_04844_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    scene_np, cam = synth.config2(args.n, args.width, args.height)
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_frame_seconds(scene_np, cam, row_stride=64)
+    times = []
+    for _ in range(args.steps):
+        secs, P, npx = oracle_frame_seconds(scene_np, cam, row_stride=64)
+        times.append(secs)
+    sec = statistics.mean(times)
+    cores = int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count())
+    val = round(1.0 / sec, 5)
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1000, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded 1M-Gaussian clustered scene)",
+            "config": {"workload": "1M Gaussians, 1920x1080, SH degree 3, QuadBox binning; FP64 CPU oracle"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: full FP64 projection, binning and sort of the frame, "
+                                       "compositing of every 64th tile row, scaled to the frame"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            from paper_2605_04844_gb300 import synth
+            scene_np, cam = synth.config2(args.n, args.width, args.height)
+            res["cpu_baseline"] = cpu_baseline(scene_np, cam)
+        line = json.dumps(res)
+        print(line, flush=True)
+        if args.out:
+            with open(args.out, "w") as f:
+                f.write(line + "\n")
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

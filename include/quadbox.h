@@ -1,0 +1,242 @@
+/*
+ * quadbox.h -- C ABI of libquadbox, a GB300 (sm_103a) tile rasteriser for
+ * 3D Gaussian Splatting with QuadBox binning and QPass traversal.
+ *
+ * Method: "QuadBox: Accelerating 3D Gaussian Splatting with Geometry-Aware
+ * Boxes" (arXiv 2605.04844).  Section/equation references below are to that
+ * paper.  Conventions the paper leaves open (near plane, Jacobian clamp, the
+ * 0.3 low-pass dilation, the 0.99 opacity cap, the 1/255 skip, the 1e-4
+ * transmittance stop, pixel centres at integer coordinates) follow the 3DGS
+ * code base the paper builds on (Sec. 4.1).
+ *
+ * General rules for every entry point:
+ *  - Pointers named d_* or documented as "device" are CUDA device pointers
+ *    owned by the caller; the library never frees them.  Structs passed by
+ *    pointer (qb_scene, qb_camera, qb_frame, ...) live in host memory.
+ *  - All work is stream-ordered on the given stream (a cudaStream_t; NULL is
+ *    the legacy default stream).  Nothing synchronises the host unless the
+ *    function says so.
+ *  - Every function returns a qb_status.  On failure qb_last_error() returns
+ *    a message for the calling thread.  No C++ exception crosses the ABI.
+ *  - Device-side failures (pair capacity exceeded, a bounded spin-wait that
+ *    ran out) are recorded in a flag word inside the workspace and reported
+ *    by the next function that synchronises (qb_frame_check, or
+ *    qb_bin_emit with a non-NULL n_pairs_out).  A kernel never writes past a
+ *    buffer because of them.
+ *  - Tiles are 16 x 16 pixels; tile id = ty * tiles_x + tx.
+ */
+#ifndef QUADBOX_H
+#define QUADBOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qb_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    QB_OK = 0,
+    QB_ERR_INVALID_ARG = 1, /* bad pointer, size, mode or alignment        */
+    QB_ERR_CUDA = 2,        /* a CUDA runtime call failed                  */
+    QB_ERR_CAPACITY = 3,    /* more Gaussian-tile pairs than pair_capacity */
+    QB_ERR_TIMEOUT = 4,     /* a device spin-wait hit its iteration limit  */
+    QB_ERR_STATE = 5        /* stages called out of order                  */
+} qb_status;
+
+/* Binning rule (how a Gaussian is mapped to tiles).
+ *  AABB3S        vanilla 3DGS square box of side 6 sqrt(lambda_max) (Sec. 2).
+ *  QUADBOX       four quadrant sub-boxes: the two along the major axis use
+ *                the AdR extents (Eq. extents-closed), the other two are
+ *                scaled by f (Eq. f-closed); tiles enumerated by QPass
+ *                (Sec. 3.1.2, Sec. 3.2).
+ *  ADR           the single opacity-aware AABB of AdR-Gaussian (Sec. 3.1.1).
+ *  QUADBOX_NAIVE QUADBOX boxes enumerated by nested loops over each sub-box
+ *                with overlap checks (the paper's QuadBox-dagger, Table 3).
+ *  DUALBOX       only the two major-axis quadrants (Sec. 3.1.2); not
+ *                conservative, images differ by design.
+ * Sub-boxes are intersected with the 3-sigma rectangle unless
+ * QB_BIN_NO_CLAMP is OR-ed into the mode; with the clamp, QUADBOX, ADR and
+ * AABB3S produce identical images. */
+typedef enum {
+    QB_BIN_AABB3S = 0,
+    QB_BIN_QUADBOX = 1,
+    QB_BIN_ADR = 2,
+    QB_BIN_QUADBOX_NAIVE = 3,
+    QB_BIN_DUALBOX = 4
+} qb_bin_mode;
+#define QB_BIN_NO_CLAMP 0x100
+
+/* Pinhole camera.  viewmat: row-major 4x4 world->view, last row (0,0,0,1);
+ * view space looks down +z.  Pixel (px, py) has its centre at
+ * (px, py) = (fx x/z + cx, fy y/z + cy); normally cx = (width-1)/2.
+ * tan_fov*: half-angle tangents (used by the Jacobian clamp).  campos: world
+ * camera centre (for view-dependent colour).  znear: Gaussians with view
+ * z <= znear are culled. */
+typedef struct {
+    float viewmat[16];
+    float fx, fy, cx, cy;
+    float tan_fovx, tan_fovy;
+    float campos[3];
+    int32_t width, height;
+    float znear;
+} qb_camera;
+
+/* Scene in structure-of-arrays form, all device float32, row-major:
+ * means [n,3]; scales [n,3] (log-scales if params_raw); quats [n,4] as
+ * (w,x,y,z), any non-zero norm; opacities [n] (logits if params_raw);
+ * sh [n,K,3] with K = (sh_degree+1)^2, sh_degree in 0..3, coefficient k
+ * ordered l*l + l + m.  Colour = max(0, sum_k sh_k Y_k(dir) + 0.5) with dir
+ * the unit vector from campos to the mean and Y_k the real spherical
+ * harmonics carrying the Condon-Shortley phase (the 3DGS basis). */
+typedef struct {
+    const float *means;
+    const float *scales;
+    const float *quats;
+    const float *opacities;
+    const float *sh;
+    int32_t n;
+    int32_t sh_degree;
+    int32_t params_raw;
+} qb_scene;
+
+/* Gradient outputs of qb_render_bwd, device float32, same shapes as the
+ * qb_scene inputs.  The callee ACCUMULATES into them (+=); the caller zeroes
+ * them first.  Gradients are w.r.t. the raw parameters when params_raw. */
+typedef struct {
+    float *means;
+    float *scales;
+    float *quats;
+    float *opacities;
+    float *sh;
+} qb_scene_grads;
+
+/* Per-frame state.  Create with qb_frame_init; the workspace is caller-
+ * allocated device memory of at least qb_frame_workspace_bytes(...) bytes,
+ * 256-byte aligned.  Fields are read-only for the caller. */
+typedef struct {
+    int32_t n, width, height, tiles_x, tiles_y;
+    uint64_t pair_capacity;
+    void *workspace;
+    size_t workspace_bytes;
+    /* written by the stages */
+    int32_t bin_mode;       /* mode used by the last qb_preprocess        */
+    int32_t sh_degree;
+    int32_t key_bits;       /* significant key bits: 31 + tile bits       */
+    int32_t stage;          /* 0 init, 1 preprocessed, 2 emitted, 3 sorted */
+    uint64_t n_pairs;       /* host copy of P when known, else UINT64_MAX  */
+    int32_t sort_digit_bits;  /* 8..11, radix digit width of qb_sort        */
+    int32_t render_batch;     /* Gaussians staged per shared-memory batch   */
+    int32_t sorted_in_alt;    /* internal: sorted pairs live in buffer 1    */
+    int32_t reserved[5];
+} qb_frame;
+
+/* Device arrays inside a frame workspace (for inspection and tests).  All
+ * per-Gaussian arrays have n entries, indexed by Gaussian. */
+typedef struct {
+    float *xy;          /* [n][2]  mu^2D in pixels                          */
+    float *conic_o;     /* [n][4]  (a, b, c, o): Lambda = [a b; b c], opacity */
+    float *rgbd;        /* [n][4]  (r, g, b, depth)                         */
+    float *box;         /* [n][4]  (x_max, y_max, f x_max, f y_max)         */
+    float *r3;          /* [n]     3-sigma radius ceil(3 sqrt(lambda_max))  */
+    int32_t *meta;      /* [n]     bit0 visible, bit1 orient (Sigma12 >= 0),
+                                   bits2-4 colour channel clamped at 0      */
+    uint32_t *counts;   /* [n]     tiles per Gaussian                       */
+    uint32_t *offsets;  /* [n]     exclusive prefix of counts               */
+    uint64_t *keys;     /* [P]     (tile << 31) | depth bits, sorted after qb_sort */
+    uint32_t *vals;     /* [P]     Gaussian index                           */
+    uint32_t *ranges;   /* [tiles][2] [start, end) into keys/vals           */
+    float *t_final;     /* [H][W]  transmittance after the last contributor */
+    int32_t *n_contrib; /* [H][W]  1 + position of the last contributor     */
+    int32_t *n_eval;    /* [H][W]  list entries the pixel evaluated before it
+                                   stopped (render statistics)               */
+    uint64_t *n_pairs;  /* [1]     P on the device                          */
+    uint32_t *err_flags;/* [1]     bit0 capacity, bit1 timeout              */
+} qb_frame_arrays;
+
+/* Thread-local description of the last failure. */
+const char *qb_last_error(void);
+
+/* Library version string. */
+const char *qb_version(void);
+
+/* Bytes of device workspace for a frame of n Gaussians, a width x height
+ * image and room for pair_capacity Gaussian-tile pairs (pair_capacity
+ * <= 2^30).  Returns 0 for invalid sizes. */
+size_t qb_frame_workspace_bytes(int32_t n, int32_t width, int32_t height, uint64_t pair_capacity);
+
+/* Binds a caller-owned workspace to *frame and resets the frame state.
+ * Errors: INVALID_ARG for bad sizes, a NULL or misaligned workspace, or
+ * workspace_bytes below qb_frame_workspace_bytes(...). */
+qb_status qb_frame_init(qb_frame *frame, int32_t n, int32_t width, int32_t height,
+                        uint64_t pair_capacity, void *d_workspace, size_t workspace_bytes,
+                        qb_stream_t stream);
+
+/* Device pointers of the frame's internal arrays. */
+qb_status qb_frame_arrays_get(const qb_frame *frame, qb_frame_arrays *out);
+
+/* Synchronises the stream and reports device-side failures recorded in the
+ * frame (CAPACITY, TIMEOUT); clears them. */
+qb_status qb_frame_check(qb_frame *frame, qb_stream_t stream);
+
+/* Stage 1 (Sec. 2 "Preprocess", Sec. 3.1): per Gaussian, EWA projection to
+ * mu^2D and the conic Lambda = (Sigma^2D)^-1 (Eq. 4), depth, SH colour, the
+ * opacity-aware threshold gamma = 2 ln(o / (1/255)) (Eq. 3, kept side),
+ * the extents x_max, y_max (Eq. extents-closed), the stretching factor f
+ * (Eq. f-closed), the 3-sigma radius, the mode's tile rectangles and the
+ * QPass tile count.  scene->n must equal frame->n; mode is a qb_bin_mode,
+ * optionally OR QB_BIN_NO_CLAMP. */
+qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, int32_t mode,
+                        qb_stream_t stream);
+
+/* Stage 2 (Sec. 2 "DuplicateWithKeys", Sec. 3.2 QPass): exclusive scan of the
+ * tile counts, then one (key, value) pair per Gaussian-tile overlap with
+ * key = (tile << 31) | float bits of the depth, value = Gaussian index,
+ * written at the Gaussian's scan offset (so pairs appear in Gaussian order).
+ * If n_pairs_out is non-NULL the host synchronises once to read P, stores it
+ * in *n_pairs_out and frame->n_pairs, and returns CAPACITY (writing no pairs)
+ * when P > pair_capacity.  With NULL nothing synchronises; an overflow is
+ * then flagged on the device and reported by qb_frame_check. */
+qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream);
+
+/* Stage 3 (Sec. 2 "SortPairs"): stable LSD radix sort of the pairs on the
+ * key bits [0, 31 + tile bits) with the library's onesweep sort, then the
+ * per-tile [start, end) ranges. */
+qb_status qb_sort(qb_frame *frame, qb_stream_t stream);
+
+/* Stage 4 (Sec. 2 "Render", Eq. 2): front-to-back compositing per pixel.
+ * bg: host float[3] background colour (NULL = black).  d_img: device
+ * float [3][height][width] (planar RGB), fully overwritten.  Also writes the
+ * frame's t_final and n_contrib, which qb_render_bwd needs. */
+qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_stream_t stream);
+
+/* Backward of stages 1 and 4 (differentiable rasteriser, Sec. 4.1): walks each
+ * tile list in reverse from every pixel's last contributor, recomputing the
+ * transmittance by division, and accumulates into grads the gradient of
+ * sum(d_dL_dimg * image) w.r.t. the scene parameters.  scene, camera and bg
+ * must be those of the forward pass.  d_dL_dimg: device float [3][H][W].
+ * If d_grad_screen is non-NULL it receives the screen-space gradients,
+ * float [n][9] = (d mu_x, d mu_y, d a, d b, d c, d o, d r, d g, d b),
+ * and must be zeroed by the caller. */
+qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, const float *bg,
+                        const float *d_dL_dimg, qb_scene_grads *grads, float *d_grad_screen,
+                        qb_stream_t stream);
+
+/* Standalone pair sort (the sort used by qb_sort): sorts n (key, value)
+ * pairs stably by key bits [0, end_bit) with the onesweep radix sort using
+ * digit_bits-wide digits (8..11).  d_keys/d_vals hold the input; the result
+ * ends in (d_keys, d_vals) if *result_in_alt is 0 on return, else in
+ * (d_keys_alt, d_vals_alt).  d_scratch: device, at least
+ * qb_sort_scratch_bytes(n, end_bit, digit_bits) bytes.  n <= 2^30. */
+size_t qb_sort_scratch_bytes(uint64_t n, int32_t end_bit, int32_t digit_bits);
+qb_status qb_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_keys_alt, uint32_t *d_vals_alt,
+                        uint64_t n, int32_t end_bit, int32_t digit_bits, void *d_scratch,
+                        size_t scratch_bytes, int32_t *result_in_alt, qb_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QUADBOX_H */

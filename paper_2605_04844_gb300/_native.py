@@ -1,0 +1,199 @@
+"""ctypes binding of libquadbox (include/quadbox.h).
+
+Argument marshalling only: every step of the rasteriser runs in the CUDA
+library.  Functions keep the C names; tensors are passed as device pointers,
+streams as ``torch.cuda.Stream.cuda_stream`` handles.  If the library is
+missing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_f = ctypes.c_float
+c_i32 = ctypes.c_int32
+c_u64 = ctypes.c_uint64
+c_vp = ctypes.c_void_p
+c_size = ctypes.c_size_t
+
+QB_OK, QB_ERR_INVALID_ARG, QB_ERR_CUDA, QB_ERR_CAPACITY, QB_ERR_TIMEOUT, QB_ERR_STATE = range(6)
+QB_BIN_AABB3S, QB_BIN_QUADBOX, QB_BIN_ADR, QB_BIN_QUADBOX_NAIVE, QB_BIN_DUALBOX = range(5)
+QB_BIN_NO_CLAMP = 0x100
+MODE_NAMES = {"aabb3s": 0, "quadbox": 1, "adr": 2, "quadbox_naive": 3, "dualbox": 4}
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "CAPACITY", 4: "TIMEOUT", 5: "STATE"}
+
+
+class QbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class QbCapacityError(QbError):
+    pass
+
+
+class QbCamera(ctypes.Structure):
+    _fields_ = [("viewmat", c_f * 16), ("fx", c_f), ("fy", c_f), ("cx", c_f), ("cy", c_f),
+                ("tan_fovx", c_f), ("tan_fovy", c_f), ("campos", c_f * 3), ("width", c_i32),
+                ("height", c_i32), ("znear", c_f)]
+
+
+class QbScene(ctypes.Structure):
+    _fields_ = [("means", c_vp), ("scales", c_vp), ("quats", c_vp), ("opacities", c_vp), ("sh", c_vp),
+                ("n", c_i32), ("sh_degree", c_i32), ("params_raw", c_i32)]
+
+
+class QbSceneGrads(ctypes.Structure):
+    _fields_ = [("means", c_vp), ("scales", c_vp), ("quats", c_vp), ("opacities", c_vp), ("sh", c_vp)]
+
+
+class QbFrame(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("width", c_i32), ("height", c_i32), ("tiles_x", c_i32), ("tiles_y", c_i32),
+                ("pair_capacity", c_u64), ("workspace", c_vp), ("workspace_bytes", c_size),
+                ("bin_mode", c_i32), ("sh_degree", c_i32), ("key_bits", c_i32), ("stage", c_i32),
+                ("n_pairs", c_u64), ("sort_digit_bits", c_i32), ("render_batch", c_i32),
+                ("sorted_in_alt", c_i32), ("reserved", c_i32 * 5)]
+
+
+class QbFrameArrays(ctypes.Structure):
+    _fields_ = [(name, c_vp) for name in ("xy", "conic_o", "rgbd", "box", "r3", "meta", "counts", "offsets",
+                                          "keys", "vals", "ranges", "t_final", "n_contrib", "n_eval", "n_pairs",
+                                          "err_flags")]
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("qb_last_error", ctypes.c_char_p, []),
+    ("qb_version", ctypes.c_char_p, []),
+    ("qb_frame_workspace_bytes", c_size, [c_i32, c_i32, c_i32, c_u64]),
+    ("qb_frame_init", c_i32, [ctypes.POINTER(QbFrame), c_i32, c_i32, c_i32, c_u64, c_vp, c_size, c_vp]),
+    ("qb_frame_arrays_get", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbFrameArrays)]),
+    ("qb_frame_check", c_i32, [ctypes.POINTER(QbFrame), c_vp]),
+    ("qb_preprocess", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera),
+                              c_i32, c_vp]),
+    ("qb_bin_emit", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(c_u64), c_vp]),
+    ("qb_sort", c_i32, [ctypes.POINTER(QbFrame), c_vp]),
+    ("qb_render_fwd", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(c_f), c_vp, c_vp]),
+    ("qb_render_bwd", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera),
+                              ctypes.POINTER(c_f), c_vp, ctypes.POINTER(QbSceneGrads), c_vp, c_vp]),
+    ("qb_sort_scratch_bytes", c_size, [c_u64, c_i32, c_i32]),
+    ("qb_sort_pairs", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, c_i32, c_vp, c_size,
+                              ctypes.POINTER(c_i32), c_vp]),
+]
+
+# Every symbol include/quadbox.h declares (checked by the CPU test suite).
+EXPORTED = [s[0] for s in _SIGS]
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libquadbox.so (building it first if allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"libquadbox not built: {_build.LIB_PATH} is missing")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB_PATH)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != QB_OK:
+        msg = load().qb_last_error().decode()
+        if status == QB_ERR_CAPACITY:
+            raise QbCapacityError(status, msg)
+        raise QbError(status, msg)
+
+
+def stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers with the C names
+# ---------------------------------------------------------------------------
+
+def qb_frame_workspace_bytes(n, width, height, pair_capacity) -> int:
+    return int(load().qb_frame_workspace_bytes(n, width, height, pair_capacity))
+
+
+def qb_frame_init(frame: QbFrame, n, width, height, pair_capacity, workspace, stream=None):
+    check(load().qb_frame_init(ctypes.byref(frame), n, width, height, pair_capacity, ptr(workspace),
+                               workspace.numel() * workspace.element_size(), stream_handle(stream)))
+
+
+def qb_frame_arrays_get(frame: QbFrame) -> QbFrameArrays:
+    out = QbFrameArrays()
+    check(load().qb_frame_arrays_get(ctypes.byref(frame), ctypes.byref(out)))
+    return out
+
+
+def qb_frame_check(frame: QbFrame, stream=None):
+    check(load().qb_frame_check(ctypes.byref(frame), stream_handle(stream)))
+
+
+def qb_preprocess(frame: QbFrame, scene: QbScene, camera: QbCamera, mode: int, stream=None):
+    check(load().qb_preprocess(ctypes.byref(frame), ctypes.byref(scene), ctypes.byref(camera), mode,
+                               stream_handle(stream)))
+
+
+def qb_bin_emit(frame: QbFrame, sync: bool = True, stream=None):
+    """Returns P when sync, else None."""
+    if sync:
+        P = c_u64(0)
+        check(load().qb_bin_emit(ctypes.byref(frame), ctypes.byref(P), stream_handle(stream)))
+        return int(P.value)
+    check(load().qb_bin_emit(ctypes.byref(frame), None, stream_handle(stream)))
+    return None
+
+
+def qb_sort(frame: QbFrame, stream=None):
+    check(load().qb_sort(ctypes.byref(frame), stream_handle(stream)))
+
+
+def _bg(bg):
+    return (c_f * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
+
+
+def qb_render_fwd(frame: QbFrame, bg, img, stream=None):
+    check(load().qb_render_fwd(ctypes.byref(frame), _bg(bg), ptr(img), stream_handle(stream)))
+
+
+def qb_render_bwd(frame: QbFrame, scene: QbScene, camera: QbCamera, bg, dL_dimg, grads: QbSceneGrads,
+                  grad_screen=None, stream=None):
+    check(load().qb_render_bwd(ctypes.byref(frame), ctypes.byref(scene), ctypes.byref(camera), _bg(bg),
+                               ptr(dL_dimg), ctypes.byref(grads), ptr(grad_screen), stream_handle(stream)))
+
+
+def qb_sort_scratch_bytes(n, end_bit, digit_bits) -> int:
+    return int(load().qb_sort_scratch_bytes(n, end_bit, digit_bits))
+
+
+def qb_sort_pairs(keys, vals, keys_alt, vals_alt, n, end_bit, digit_bits, scratch, stream=None) -> bool:
+    """Returns True when the result is in the *_alt buffers."""
+    alt = c_i32(0)
+    check(load().qb_sort_pairs(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt), n, end_bit, digit_bits,
+                               ptr(scratch), scratch.numel() * scratch.element_size(), ctypes.byref(alt),
+                               stream_handle(stream)))
+    return bool(alt.value)

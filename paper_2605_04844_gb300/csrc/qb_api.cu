@@ -1,0 +1,429 @@
+// qb_api.cu -- the extern "C" entry points of libquadbox (include/quadbox.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "qb_kernels.cuh"
+
+using namespace qb;
+
+namespace {
+
+thread_local std::string g_err;
+
+qb_status fail(qb_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define QB_CUDA(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(QB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int tile_bits_for(int tiles) {
+    int b = 0;
+    while ((1ll << b) < (long long)tiles) ++b;
+    return b;
+}
+
+bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
+    if (n < 0 || W <= 0 || H <= 0 || W > (1 << 15) || H > (1 << 15) || cap > (1ull << 30)) return false;
+    const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    const int tiles = tx * ty;
+    const int key_bits = kDepthBits + tile_bits_for(tiles);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t N = (size_t)n;
+    L.xy = take(8 * N);
+    L.conic_o = take(16 * N);
+    L.rgbd = take(16 * N);
+    L.box = take(16 * N);
+    L.r3 = take(4 * N);
+    L.meta = take(4 * N);
+    L.counts = take(4 * N);
+    L.offsets = take(4 * N);
+    L.scan_part = take(8 * scan_partials_count(n));
+    L.keys0 = take(8 * cap);
+    L.keys1 = take(8 * cap);
+    L.vals0 = take(4 * cap);
+    L.vals1 = take(4 * cap);
+    size_t sb = 0;
+    for (int d = 8; d <= kMaxDigitBits; ++d) {
+        size_t b = sort_scratch_bytes(cap, key_bits, d);
+        if (b > sb) sb = b;
+    }
+    L.sort_scratch_bytes = sb;
+    L.sort_scratch = take(sb);
+    L.ranges = take(8 * (size_t)tiles);
+    L.tfinal = take(4 * (size_t)W * H);
+    L.ncontrib = take(4 * (size_t)W * H);
+    L.neval = take(4 * (size_t)W * H);
+    L.gscreen = take(36 * N);
+    L.state = take(256);
+    L.total = off;
+    return true;
+}
+
+template <typename T>
+T *at(const qb_frame *f, size_t off) {
+    return reinterpret_cast<T *>(static_cast<uint8_t *>(f->workspace) + off);
+}
+
+CamDev to_cam(const qb_camera &c) {
+    CamDev d;
+    for (int i = 0; i < 12; ++i) d.V[i] = c.viewmat[i];
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    d.limx = 1.3f * c.tan_fovx;
+    d.limy = 1.3f * c.tan_fovy;
+    d.campos[0] = c.campos[0];
+    d.campos[1] = c.campos[1];
+    d.campos[2] = c.campos[2];
+    d.znear = c.znear;
+    d.W = c.width;
+    d.H = c.height;
+    return d;
+}
+
+qb_status check_frame(const qb_frame *f, Layout &L) {
+    if (!f || !f->workspace) return fail(QB_ERR_INVALID_ARG, "frame is NULL or not initialised");
+    if (!make_layout(f->n, f->width, f->height, f->pair_capacity, L))
+        return fail(QB_ERR_INVALID_ARG, "frame has invalid sizes");
+    return QB_OK;
+}
+
+qb_status check_scene(const qb_frame *f, const qb_scene *s) {
+    if (!s) return fail(QB_ERR_INVALID_ARG, "scene is NULL");
+    if (s->n != f->n) return fail(QB_ERR_INVALID_ARG, "scene.n (%d) != frame.n (%d)", s->n, f->n);
+    if (s->sh_degree < 0 || s->sh_degree > 3) return fail(QB_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (s->n > 0 && (!s->means || !s->scales || !s->quats || !s->opacities || !s->sh))
+        return fail(QB_ERR_INVALID_ARG, "scene has a NULL array");
+    return QB_OK;
+}
+
+qb_status check_camera(const qb_frame *f, const qb_camera *c) {
+    if (!c) return fail(QB_ERR_INVALID_ARG, "camera is NULL");
+    if (c->width != f->width || c->height != f->height)
+        return fail(QB_ERR_INVALID_ARG, "camera size %dx%d != frame size %dx%d", c->width, c->height, f->width,
+                    f->height);
+    if (!(c->fx > 0.f) || !(c->fy > 0.f) || !(c->tan_fovx > 0.f) || !(c->tan_fovy > 0.f))
+        return fail(QB_ERR_INVALID_ARG, "camera focal lengths and fov tangents must be positive");
+    return QB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qb_last_error(void) { return g_err.c_str(); }
+
+const char *qb_version(void) { return "libquadbox 0.1 sm_103a"; }
+
+size_t qb_frame_workspace_bytes(int32_t n, int32_t width, int32_t height, uint64_t pair_capacity) {
+    Layout L;
+    if (!make_layout(n, width, height, pair_capacity, L)) return 0;
+    return L.total;
+}
+
+qb_status qb_frame_init(qb_frame *frame, int32_t n, int32_t width, int32_t height, uint64_t pair_capacity,
+                        void *d_workspace, size_t workspace_bytes, qb_stream_t stream) {
+    if (!frame) return fail(QB_ERR_INVALID_ARG, "frame is NULL");
+    Layout L;
+    if (!make_layout(n, width, height, pair_capacity, L))
+        return fail(QB_ERR_INVALID_ARG, "invalid frame sizes n=%d %dx%d capacity=%llu", n, width, height,
+                    (unsigned long long)pair_capacity);
+    if (!d_workspace) return fail(QB_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+        return fail(QB_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (workspace_bytes < L.total)
+        return fail(QB_ERR_INVALID_ARG, "workspace too small: %zu < %zu", workspace_bytes, L.total);
+    std::memset(frame, 0, sizeof(*frame));
+    frame->n = n;
+    frame->width = width;
+    frame->height = height;
+    frame->tiles_x = (width + kTile - 1) / kTile;
+    frame->tiles_y = (height + kTile - 1) / kTile;
+    frame->pair_capacity = pair_capacity;
+    frame->workspace = d_workspace;
+    frame->workspace_bytes = workspace_bytes;
+    frame->key_bits = kDepthBits + tile_bits_for(frame->tiles_x * frame->tiles_y);
+    frame->n_pairs = UINT64_MAX;
+    frame->sort_digit_bits = 8;
+    frame->render_batch = 256;
+    QB_CUDA(cudaMemsetAsync(at<uint8_t>(frame, L.state), 0, 256, (cudaStream_t)stream));
+    return QB_OK;
+}
+
+qb_status qb_frame_arrays_get(const qb_frame *frame, qb_frame_arrays *out) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    if (!out) return fail(QB_ERR_INVALID_ARG, "out is NULL");
+    const bool alt = frame->sorted_in_alt != 0 && frame->stage >= 3;
+    out->xy = at<float>(frame, L.xy);
+    out->conic_o = at<float>(frame, L.conic_o);
+    out->rgbd = at<float>(frame, L.rgbd);
+    out->box = at<float>(frame, L.box);
+    out->r3 = at<float>(frame, L.r3);
+    out->meta = at<int32_t>(frame, L.meta);
+    out->counts = at<uint32_t>(frame, L.counts);
+    out->offsets = at<uint32_t>(frame, L.offsets);
+    out->keys = at<uint64_t>(frame, alt ? L.keys1 : L.keys0);
+    out->vals = at<uint32_t>(frame, alt ? L.vals1 : L.vals0);
+    out->ranges = at<uint32_t>(frame, L.ranges);
+    out->t_final = at<float>(frame, L.tfinal);
+    out->n_contrib = at<int32_t>(frame, L.ncontrib);
+    out->n_eval = at<int32_t>(frame, L.neval);
+    out->n_pairs = at<uint64_t>(frame, L.state);
+    out->err_flags = at<uint32_t>(frame, L.state + 8);
+    return QB_OK;
+}
+
+qb_status qb_frame_check(qb_frame *frame, qb_stream_t stream) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    uint32_t flags = 0;
+    QB_CUDA(cudaMemcpyAsync(&flags, at<uint32_t>(frame, L.state + 8), 4, cudaMemcpyDeviceToHost,
+                            (cudaStream_t)stream));
+    QB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (flags) QB_CUDA(cudaMemsetAsync(at<uint32_t>(frame, L.state + 8), 0, 4, (cudaStream_t)stream));
+    if (flags & kErrCapacity) return fail(QB_ERR_CAPACITY, "pair capacity exceeded on the device");
+    if (flags & kErrTimeout) return fail(QB_ERR_TIMEOUT, "a device spin-wait reached its iteration limit");
+    return QB_OK;
+}
+
+qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, int32_t mode,
+                        qb_stream_t stream) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    if ((st = check_scene(frame, scene)) != QB_OK) return st;
+    if ((st = check_camera(frame, camera)) != QB_OK) return st;
+    const int base_mode = mode & 0xff;
+    if (base_mode < QB_BIN_AABB3S || base_mode > QB_BIN_DUALBOX || (mode & ~(0xff | QB_BIN_NO_CLAMP)))
+        return fail(QB_ERR_INVALID_ARG, "invalid binning mode %d", mode);
+    PreArgs a;
+    a.n = scene->n;
+    a.means = scene->means;
+    a.scales = scene->scales;
+    a.quats = scene->quats;
+    a.opac = scene->opacities;
+    a.sh = scene->sh;
+    a.raw = scene->params_raw != 0;
+    a.cam = to_cam(*camera);
+    a.mode = base_mode;
+    a.clamp3s = (mode & QB_BIN_NO_CLAMP) == 0;
+    a.xy = at<float2>(frame, L.xy);
+    a.conic_o = at<float4>(frame, L.conic_o);
+    a.rgbd = at<float4>(frame, L.rgbd);
+    a.box = at<float4>(frame, L.box);
+    a.r3 = at<float>(frame, L.r3);
+    a.meta = at<int>(frame, L.meta);
+    a.counts = at<uint32_t>(frame, L.counts);
+    QB_CUDA(launch_preprocess(a, scene->sh_degree, (cudaStream_t)stream));
+    frame->bin_mode = mode;
+    frame->sh_degree = scene->sh_degree;
+    frame->stage = 1;
+    frame->n_pairs = UINT64_MAX;
+    return QB_OK;
+}
+
+qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    if (frame->stage < 1) return fail(QB_ERR_STATE, "qb_bin_emit before qb_preprocess");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t *d_np = at<uint64_t>(frame, L.state);
+    QB_CUDA(launch_scan(at<uint32_t>(frame, L.counts), frame->n, at<uint32_t>(frame, L.offsets),
+                        at<uint64_t>(frame, L.scan_part), d_np, s));
+    frame->n_pairs = UINT64_MAX;
+    if (n_pairs_out) {
+        uint64_t P = 0;
+        QB_CUDA(cudaMemcpyAsync(&P, d_np, sizeof(P), cudaMemcpyDeviceToHost, s));
+        QB_CUDA(cudaStreamSynchronize(s));
+        *n_pairs_out = P;
+        if (P > frame->pair_capacity) {
+            frame->stage = 1;
+            return fail(QB_ERR_CAPACITY, "%llu pairs exceed the capacity of %llu", (unsigned long long)P,
+                        (unsigned long long)frame->pair_capacity);
+        }
+        frame->n_pairs = P;
+    }
+    EmitArgs a;
+    a.n = frame->n;
+    a.xy = at<float2>(frame, L.xy);
+    a.box = at<float4>(frame, L.box);
+    a.r3 = at<float>(frame, L.r3);
+    a.meta = at<int>(frame, L.meta);
+    a.rgbd = at<float4>(frame, L.rgbd);
+    a.counts = at<uint32_t>(frame, L.counts);
+    a.offsets = at<uint32_t>(frame, L.offsets);
+    a.keys = at<uint64_t>(frame, L.keys0);
+    a.vals = at<uint32_t>(frame, L.vals0);
+    a.n_pairs = d_np;
+    a.capacity = frame->pair_capacity;
+    a.mode = frame->bin_mode & 0xff;
+    a.clamp3s = (frame->bin_mode & QB_BIN_NO_CLAMP) == 0;
+    a.W = frame->width;
+    a.H = frame->height;
+    a.tiles_x = frame->tiles_x;
+    a.err = at<uint32_t>(frame, L.state + 8);
+    QB_CUDA(launch_emit(a, s));
+    frame->stage = 2;
+    return QB_OK;
+}
+
+qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    if (frame->stage < 2) return fail(QB_ERR_STATE, "qb_sort before qb_bin_emit");
+    if (frame->sort_digit_bits < 8 || frame->sort_digit_bits > kMaxDigitBits)
+        return fail(QB_ERR_INVALID_ARG, "sort_digit_bits must be 8..11");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool known = frame->n_pairs != UINT64_MAX;
+    const uint64_t n_max = known ? frame->n_pairs : frame->pair_capacity;
+    const uint64_t *n_dev = known ? nullptr : at<uint64_t>(frame, L.state);
+    int passes = 0;
+    QB_CUDA(sort_pairs(at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint64_t>(frame, L.keys1),
+                       at<uint32_t>(frame, L.vals1), n_max, n_dev, frame->key_bits, frame->sort_digit_bits,
+                       at<void>(frame, L.sort_scratch), at<uint32_t>(frame, L.state + 8), s, &passes));
+    frame->sorted_in_alt = passes & 1;
+    const uint64_t *sorted = at<uint64_t>(frame, frame->sorted_in_alt ? L.keys1 : L.keys0);
+    QB_CUDA(launch_ranges(sorted, n_max, n_dev, at<uint2>(frame, L.ranges), frame->tiles_x * frame->tiles_y, s));
+    frame->stage = 3;
+    return QB_OK;
+}
+
+qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_stream_t stream) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    if (frame->stage < 3) return fail(QB_ERR_STATE, "qb_render_fwd before qb_sort");
+    if (!d_img) return fail(QB_ERR_INVALID_ARG, "image pointer is NULL");
+    RenderArgs a;
+    a.ranges = at<uint2>(frame, L.ranges);
+    a.vals = at<uint32_t>(frame, frame->sorted_in_alt ? L.vals1 : L.vals0);
+    a.xy = at<float2>(frame, L.xy);
+    a.conic_o = at<float4>(frame, L.conic_o);
+    a.rgbd = at<float4>(frame, L.rgbd);
+    a.W = frame->width;
+    a.H = frame->height;
+    a.tiles_x = frame->tiles_x;
+    a.tiles_y = frame->tiles_y;
+    for (int c = 0; c < 3; ++c) a.bg[c] = bg ? bg[c] : 0.f;
+    a.img = d_img;
+    a.tfinal = at<float>(frame, L.tfinal);
+    a.ncontrib = at<int>(frame, L.ncontrib);
+    a.neval = at<int>(frame, L.neval);
+    QB_CUDA(launch_render(a, frame->render_batch, (cudaStream_t)stream));
+    frame->stage = 4;
+    return QB_OK;
+}
+
+qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, const float *bg,
+                        const float *d_dL_dimg, qb_scene_grads *grads, float *d_grad_screen, qb_stream_t stream) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    if (frame->stage < 4) return fail(QB_ERR_STATE, "qb_render_bwd before qb_render_fwd");
+    if ((st = check_scene(frame, scene)) != QB_OK) return st;
+    if ((st = check_camera(frame, camera)) != QB_OK) return st;
+    if (scene->sh_degree != frame->sh_degree) return fail(QB_ERR_INVALID_ARG, "sh_degree differs from forward");
+    if (!d_dL_dimg || !grads) return fail(QB_ERR_INVALID_ARG, "dL_dimg or grads is NULL");
+    if (frame->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
+        return fail(QB_ERR_INVALID_ARG, "a gradient array is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    float *gscreen = d_grad_screen;
+    if (!gscreen) {
+        gscreen = at<float>(frame, L.gscreen);
+        QB_CUDA(cudaMemsetAsync(gscreen, 0, 36 * (size_t)frame->n, s));
+    }
+    BwdArgs b;
+    b.ranges = at<uint2>(frame, L.ranges);
+    b.vals = at<uint32_t>(frame, frame->sorted_in_alt ? L.vals1 : L.vals0);
+    b.xy = at<float2>(frame, L.xy);
+    b.conic_o = at<float4>(frame, L.conic_o);
+    b.rgbd = at<float4>(frame, L.rgbd);
+    b.W = frame->width;
+    b.H = frame->height;
+    b.tiles_x = frame->tiles_x;
+    b.tiles_y = frame->tiles_y;
+    for (int c = 0; c < 3; ++c) b.bg[c] = bg ? bg[c] : 0.f;
+    b.dL_dimg = d_dL_dimg;
+    b.tfinal = at<float>(frame, L.tfinal);
+    b.ncontrib = at<int>(frame, L.ncontrib);
+    b.g_screen = gscreen;
+    QB_CUDA(launch_render_bwd(b, s));
+    PreBwdArgs p;
+    p.n = scene->n;
+    p.means = scene->means;
+    p.scales = scene->scales;
+    p.quats = scene->quats;
+    p.opac = scene->opacities;
+    p.sh = scene->sh;
+    p.raw = scene->params_raw != 0;
+    p.cam = to_cam(*camera);
+    p.meta = at<int>(frame, L.meta);
+    p.g_screen = gscreen;
+    p.gm = grads->means;
+    p.gs = grads->scales;
+    p.gq = grads->quats;
+    p.go = grads->opacities;
+    p.gsh = grads->sh;
+    QB_CUDA(launch_preprocess_bwd(p, scene->sh_degree, s));
+    return QB_OK;
+}
+
+size_t qb_sort_scratch_bytes(uint64_t n, int32_t end_bit, int32_t digit_bits) {
+    if (n > (1ull << 30)) return 0;
+    size_t b = sort_scratch_bytes(n, end_bit, digit_bits);
+    return b ? b + 256 : 0;  // + the error word
+}
+
+qb_status qb_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_keys_alt, uint32_t *d_vals_alt, uint64_t n,
+                        int32_t end_bit, int32_t digit_bits, void *d_scratch, size_t scratch_bytes,
+                        int32_t *result_in_alt, qb_stream_t stream) {
+    if (n > (1ull << 30)) return fail(QB_ERR_INVALID_ARG, "n must be <= 2^30");
+    if (digit_bits < 8 || digit_bits > kMaxDigitBits) return fail(QB_ERR_INVALID_ARG, "digit_bits must be 8..11");
+    if (end_bit < 1 || end_bit > 64) return fail(QB_ERR_INVALID_ARG, "end_bit must be 1..64");
+    if (!result_in_alt) return fail(QB_ERR_INVALID_ARG, "result_in_alt is NULL");
+    size_t need = qb_sort_scratch_bytes(n, end_bit, digit_bits);
+    if (need == 0) return fail(QB_ERR_INVALID_ARG, "unsupported sort configuration");
+    if (n > 0 && (!d_keys || !d_vals || !d_keys_alt || !d_vals_alt || !d_scratch))
+        return fail(QB_ERR_INVALID_ARG, "NULL buffer");
+    if (scratch_bytes < need) return fail(QB_ERR_INVALID_ARG, "scratch too small: %zu < %zu", scratch_bytes, need);
+    if (reinterpret_cast<uintptr_t>(d_scratch) % 256 != 0)
+        return fail(QB_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t *base = static_cast<uint8_t *>(d_scratch);
+    uint32_t *err = reinterpret_cast<uint32_t *>(base + need - 256);
+    QB_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    int passes = 0;
+    QB_CUDA(sort_pairs(d_keys, d_vals, d_keys_alt, d_vals_alt, n, nullptr, end_bit, digit_bits, d_scratch, err, s,
+                       &passes));
+    *result_in_alt = passes & 1;
+    uint32_t flags = 0;
+    QB_CUDA(cudaMemcpyAsync(&flags, err, 4, cudaMemcpyDeviceToHost, s));
+    QB_CUDA(cudaStreamSynchronize(s));
+    if (flags & kErrTimeout) return fail(QB_ERR_TIMEOUT, "sort look-back reached its iteration limit");
+    return QB_OK;
+}
+
+}  // extern "C"

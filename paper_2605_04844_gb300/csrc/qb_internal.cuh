@@ -1,0 +1,214 @@
+// qb_internal.cuh -- shared device helpers and workspace layout of libquadbox.
+// Method: QuadBox (arXiv 2605.04844); see include/quadbox.h for the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/quadbox.h"
+
+namespace qb {
+
+constexpr int kTile = 16;             // 16 x 16 pixel tiles (Sec. 2)
+constexpr int kTileShift = 4;
+constexpr float kAlphaMin = 1.0f / 255.0f;  // alpha_min (Sec. 3.1.1)
+constexpr float kAlphaMax = 0.99f;          // opacity cap (3DGS convention)
+constexpr float kTStop = 1e-4f;             // transmittance stop (3DGS convention)
+constexpr float kDilation = 0.3f;           // low-pass dilation of Sigma^2D
+constexpr int kDepthBits = 31;              // key = (tile << 31) | depth bits
+constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr int kMaxDigitBits = 11;
+constexpr int kMaxPasses = 8;              // ceil(64 / 8)
+
+// meta bits
+constexpr int kMetaVisible = 1;
+constexpr int kMetaOrient = 2;
+constexpr int kMetaClampShift = 2;
+
+struct CamDev {
+    float V[12];  // rows 0..2 of the world->view matrix
+    float fx, fy, cx, cy;
+    float limx, limy;  // 1.3 * tan_fov
+    float campos[3];
+    float znear;
+    int W, H;
+};
+
+// Workspace offsets (bytes) of a frame; all 256-byte aligned.
+struct Layout {
+    size_t xy, conic_o, rgbd, box, r3, meta, counts, offsets;
+    size_t scan_part;
+    size_t keys0, keys1, vals0, vals1;
+    size_t sort_scratch, sort_scratch_bytes;
+    size_t ranges, tfinal, ncontrib, neval;
+    size_t gscreen;  // [n][9] screen-space gradients
+    size_t state;  // u64 n_pairs, u32 err_flags, padding
+    size_t total;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---- sort -------------------------------------------------------------------
+size_t sort_scratch_bytes(uint64_t n, int end_bit, int digit_bits);
+// Sorts pairs on bits [0, end_bit).  n_dev: device count (<= n_max) or null
+// when n_max is exact.  Returns the number of passes; result lies in the alt
+// buffers when the pass count is odd.
+cudaError_t sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                       uint64_t n_max, const uint64_t *n_dev, int end_bit, int digit_bits,
+                       void *scratch, uint32_t *err_flags, cudaStream_t stream, int *passes_out);
+
+// ---- device helpers -----------------------------------------------------------
+// Exponent of the 2D Gaussian at offset (dx, dy) = mu^2D - pixel:
+// -(a dx^2 + c dy^2)/2 - b dx dy.  The operation sequence is spelled out with
+// intrinsics so the forward and backward kernels take identical decisions.
+__device__ __forceinline__ float eval_power(const float4 &co, float dx, float dy) {
+    const float dxdx = __fmul_rn(dx, dx), dydy = __fmul_rn(dy, dy), dxdy = __fmul_rn(dx, dy);
+    const float s = fmaf(co.x, dxdx, __fmul_rn(co.z, dydy));
+    return fmaf(-0.5f, s, -__fmul_rn(co.y, dxdy));
+}
+
+struct Rect {
+    int x0, y0, x1, y1;  // inclusive tile bounds; empty if x0 > x1 || y0 > y1
+};
+
+__device__ __forceinline__ bool rect_empty(const Rect &r) { return r.x0 > r.x1 || r.y0 > r.y1; }
+
+__device__ __forceinline__ Rect empty_rect() { return Rect{1, 1, 0, 0}; }
+
+// Closed pixel interval [lo, hi] -> tiles of the pixel centres it holds,
+// clipped to [0, npx-1].  Single IEEE float operations only (no contraction
+// is possible: no products), so the integers are reproducible off-device.
+__device__ __forceinline__ bool tiles_of(float lo, float hi, int npx, int &t0, int &t1) {
+    float p0 = fmaxf(ceilf(lo), 0.0f);
+    float p1 = fminf(floorf(hi), (float)(npx - 1));
+    if (!(p0 <= p1)) return false;
+    t0 = ((int)p0) >> kTileShift;
+    t1 = ((int)p1) >> kTileShift;
+    return true;
+}
+
+__device__ __forceinline__ Rect intersect(const Rect &a, const Rect &b) {
+    Rect r{max(a.x0, b.x0), max(a.y0, b.y0), min(a.x1, b.x1), min(a.y1, b.y1)};
+    return rect_empty(r) ? empty_rect() : r;
+}
+
+// The per-mode tile rectangles of one Gaussian (up to four sub-boxes).
+// Quadrant order I (+x,+y), II (-x,+y), III (-x,-y), IV (+x,-y); orient = 1
+// when Sigma12 >= 0, i.e. the major axis runs through quadrants I and III.
+// Sub-boxes share the corner mu^2D (Sec. 3.1.2).
+__device__ __forceinline__ int box_rects(float mx, float my, float4 box, float r3, bool orient, int mode,
+                                         bool clamp3s, int W, int H, Rect out[4]) {
+    out[0] = out[1] = out[2] = out[3] = empty_rect();
+    Rect r3s;
+    // __fadd_rn/__fsub_rn: one rounding each, never fused with a product.
+    bool ok = tiles_of(__fsub_rn(ceilf(mx), r3), __fadd_rn(floorf(mx), r3), W, r3s.x0, r3s.x1) &
+              tiles_of(__fsub_rn(ceilf(my), r3), __fadd_rn(floorf(my), r3), H, r3s.y0, r3s.y1);
+    if (!ok) r3s = empty_rect();
+    if (mode == QB_BIN_AABB3S) {
+        out[0] = r3s;
+        return rect_empty(r3s) ? 0 : 1;
+    }
+    if (clamp3s && rect_empty(r3s)) return 0;
+    if (mode == QB_BIN_ADR) {
+        Rect r;
+        bool oka = tiles_of(__fsub_rn(mx, box.x), __fadd_rn(mx, box.x), W, r.x0, r.x1) &
+                   tiles_of(__fsub_rn(my, box.y), __fadd_rn(my, box.y), H, r.y0, r.y1);
+        if (!oka) return 0;
+        out[0] = clamp3s ? intersect(r, r3s) : r;
+        return rect_empty(out[0]) ? 0 : 1;
+    }
+    int nonempty = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        bool same = (q == 0 || q == 2);
+        bool major = orient ? same : !same;
+        if (mode == QB_BIN_DUALBOX && !major) continue;
+        float ex = major ? box.x : box.z, ey = major ? box.y : box.w;
+        bool px = (q == 0 || q == 3), py = (q == 0 || q == 1);
+        float xlo = px ? mx : __fsub_rn(mx, ex), xhi = px ? __fadd_rn(mx, ex) : mx;
+        float ylo = py ? my : __fsub_rn(my, ey), yhi = py ? __fadd_rn(my, ey) : my;
+        Rect r;
+        bool okq = tiles_of(xlo, xhi, W, r.x0, r.x1) & tiles_of(ylo, yhi, H, r.y0, r.y1);
+        if (!okq) continue;
+        out[q] = clamp3s ? intersect(r, r3s) : r;
+        nonempty += rect_empty(out[q]) ? 0 : 1;
+    }
+    return nonempty;
+}
+
+// QPass (Sec. 3.2): global tile range of the sub-boxes, scan lines along its
+// shorter axis; per line, min/max merge of the other-axis ranges of the
+// sub-boxes whose range overlaps the line.  Returns the number of lines and
+// the scan geometry; line_interval() gives a line's [lo, hi].
+struct QPass {
+    Rect b[4];
+    int s0, s1;    // scan-line range
+    bool columns;  // true: lines are tile columns (x), intervals along y
+};
+
+__device__ __forceinline__ bool qpass_setup(const Rect rects[4], QPass &qp) {
+    int gx0 = 1 << 30, gy0 = 1 << 30, gx1 = -1, gy1 = -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        qp.b[q] = rects[q];
+        if (rect_empty(rects[q])) continue;
+        gx0 = min(gx0, rects[q].x0);
+        gy0 = min(gy0, rects[q].y0);
+        gx1 = max(gx1, rects[q].x1);
+        gy1 = max(gy1, rects[q].y1);
+    }
+    if (gx1 < 0) return false;
+    qp.columns = (gx1 - gx0) <= (gy1 - gy0);
+    qp.s0 = qp.columns ? gx0 : gy0;
+    qp.s1 = qp.columns ? gx1 : gy1;
+    return true;
+}
+
+__device__ __forceinline__ void qpass_line(const QPass &qp, int s, int &lo, int &hi) {
+    lo = 1 << 30;
+    hi = -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const Rect &r = qp.b[q];
+        int a0 = qp.columns ? r.x0 : r.y0, a1 = qp.columns ? r.x1 : r.y1;
+        int o0 = qp.columns ? r.y0 : r.x0, o1 = qp.columns ? r.y1 : r.x1;
+        bool hit = (s >= a0) & (s <= a1);  // empty boxes have a0 > a1
+        lo = hit ? min(lo, o0) : lo;
+        hi = hit ? max(hi, o1) : hi;
+    }
+}
+
+__device__ __forceinline__ uint32_t qpass_count(const Rect rects[4]) {
+    QPass qp;
+    if (!qpass_setup(rects, qp)) return 0;
+    uint32_t c = 0;
+    for (int s = qp.s0; s <= qp.s1; ++s) {
+        int lo, hi;
+        qpass_line(qp, s, lo, hi);
+        c += (hi >= lo) ? (uint32_t)(hi - lo + 1) : 0u;
+    }
+    return c;
+}
+
+// Naive traversal (QuadBox-dagger, Table 3): nested loops over each
+// sub-box's rectangle, skipping tiles held by an earlier sub-box.
+__device__ __forceinline__ bool in_rect(const Rect &r, int tx, int ty) {
+    return !rect_empty(r) && tx >= r.x0 && tx <= r.x1 && ty >= r.y0 && ty <= r.y1;
+}
+
+__device__ __forceinline__ uint32_t naive_count(const Rect r[4]) {
+    uint32_t c = 0;
+    for (int q = 0; q < 4; ++q) {
+        if (rect_empty(r[q])) continue;
+        for (int ty = r[q].y0; ty <= r[q].y1; ++ty)
+            for (int tx = r[q].x0; tx <= r[q].x1; ++tx) {
+                bool seen = false;
+                for (int p = 0; p < q; ++p) seen |= in_rect(r[p], tx, ty);
+                c += seen ? 0u : 1u;
+            }
+    }
+    return c;
+}
+
+}  // namespace qb

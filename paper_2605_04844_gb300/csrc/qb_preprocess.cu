@@ -1,0 +1,90 @@
+// qb_preprocess.cu -- K1: Gaussian-parallel preprocess (Sec. 2 "Preprocess",
+// Sec. 3.1 QuadBox construction, Sec. 3.2 QPass count).
+//
+// One thread per Gaussian.  Reads the raw parameters (44 B + 12 (deg+1)^2 B),
+// writes mu^2D, conic+opacity, colour+depth, the box record, the 3-sigma
+// radius, a meta word and the tile count (68 B).  Culled Gaussians write only
+// their count and meta word and skip the SH read.
+#include "qb_kernels.cuh"
+#include "qb_project.cuh"
+
+namespace qb {
+
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const CamDev &cam = a.cam;
+    const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
+    Proj p;
+    bool ok = project_gaussian(cam, m0, m1, m2, a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2],
+                               a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3],
+                               a.raw, p);
+    if (ok) {
+        float ov = a.opac[i];
+        p.o = a.raw ? 1.0f / (1.0f + expf(-ov)) : ov;
+        ok = p.o >= kAlphaMin;  // no pixel of this Gaussian reaches alpha_min
+    }
+    if (!ok) {
+        a.counts[i] = 0u;
+        a.meta[i] = 0;
+        return;
+    }
+    BoxTerms bt = box_terms(p);
+
+    // view-dependent colour
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float dx = m0 - cam.campos[0], dy = m1 - cam.campos[1], dz = m2 - cam.campos[2];
+    float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    float Y[16];
+    sh_eval<DEG>(dx * inv, dy * inv, dz * inv, Y);
+    const float *sh = a.sh + (size_t)i * (K * 3);
+    float rgb[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        rgb[0] = fmaf(Y[k], __ldg(sh + 3 * k), rgb[0]);
+        rgb[1] = fmaf(Y[k], __ldg(sh + 3 * k + 1), rgb[1]);
+        rgb[2] = fmaf(Y[k], __ldg(sh + 3 * k + 2), rgb[2]);
+    }
+    int meta = kMetaVisible | (bt.orient ? kMetaOrient : 0);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        if (rgb[ch] < 0.f) {
+            meta |= 1 << (kMetaClampShift + ch);
+            rgb[ch] = 0.f;
+        }
+    }
+
+    Rect rects[4];
+    box_rects(p.mx, p.my, bt.box, bt.r3, bt.orient, a.mode, a.clamp3s, cam.W, cam.H, rects);
+    uint32_t cnt;
+    if (a.mode == QB_BIN_AABB3S || a.mode == QB_BIN_ADR) {
+        cnt = rect_empty(rects[0]) ? 0u : (uint32_t)((rects[0].x1 - rects[0].x0 + 1) * (rects[0].y1 - rects[0].y0 + 1));
+    } else if (a.mode == QB_BIN_QUADBOX_NAIVE) {
+        cnt = naive_count(rects);
+    } else {
+        cnt = qpass_count(rects);
+    }
+
+    a.xy[i] = make_float2(p.mx, p.my);
+    a.conic_o[i] = make_float4(p.a, p.b, p.c, p.o);
+    a.rgbd[i] = make_float4(rgb[0], rgb[1], rgb[2], p.tz);
+    a.box[i] = bt.box;
+    a.r3[i] = bt.r3;
+    a.meta[i] = meta;
+    a.counts[i] = cnt;
+}
+
+cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    dim3 grid((a.n + 255) / 256), block(256);
+    switch (deg) {
+    case 0: preprocess_kernel<0><<<grid, block, 0, s>>>(a); break;
+    case 1: preprocess_kernel<1><<<grid, block, 0, s>>>(a); break;
+    case 2: preprocess_kernel<2><<<grid, block, 0, s>>>(a); break;
+    default: preprocess_kernel<3><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qb
