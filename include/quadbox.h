@@ -235,6 +235,27 @@ qb_status qb_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_keys_alt
                         uint64_t n, int32_t end_bit, int32_t digit_bits, void *d_scratch,
                         size_t scratch_bytes, int32_t *result_in_alt, qb_stream_t stream);
 
+/* The same sort for callers that may not allocate device memory (no
+ * counterpart in the paper).  Some callers cannot call cudaMalloc: a plug-in
+ * whose host application owns all device memory, a render loop that must not
+ * stall on an allocation, code that must keep a fixed device footprint.
+ * Here the scratch lives in a fixed 16 MiB __device__ array inside the
+ * library (qb_sort_pairs_noalloc_max_scratch() bytes), which every GPU that
+ * loads the library holds until the process exits; no call allocates or
+ * frees memory.  Sizes whose scratch (qb_sort_scratch_bytes(n, end_bit,
+ * digit_bits) minus 256) exceeds that array are rejected with INVALID_ARG,
+ * e.g. more than about 11M pairs at 44 key bits with 8-bit digits.
+ * Arguments and result as for qb_sort_pairs.  The first call on a device
+ * looks up the array's device address; make it before any stream capture.
+ * All calls share the one array, and each call clears what must start at
+ * zero, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race with each other: serialise them.  Synchronises the stream
+ * once, like qb_sort_pairs. */
+size_t qb_sort_pairs_noalloc_max_scratch(void);
+qb_status qb_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_keys_alt, uint32_t *d_vals_alt,
+                                uint64_t n, int32_t end_bit, int32_t digit_bits, int32_t *result_in_alt,
+                                qb_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ _SIGS = [
     ("qb_sort_scratch_bytes", c_size, [c_u64, c_i32, c_i32]),
     ("qb_sort_pairs", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, c_i32, c_vp, c_size,
                               ctypes.POINTER(c_i32), c_vp]),
+    ("qb_sort_pairs_noalloc_max_scratch", c_size, []),
+    ("qb_sort_pairs_noalloc", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, c_i32, ctypes.POINTER(c_i32), c_vp]),
 ]
 
 # Every symbol include/quadbox.h declares (checked by the CPU test suite).
@@ -196,4 +198,13 @@ def qb_sort_pairs(keys, vals, keys_alt, vals_alt, n, end_bit, digit_bits, scratc
     check(load().qb_sort_pairs(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt), n, end_bit, digit_bits,
                                ptr(scratch), scratch.numel() * scratch.element_size(), ctypes.byref(alt),
                                stream_handle(stream)))
+    return bool(alt.value)
+
+
+def qb_sort_pairs_noalloc(keys, vals, keys_alt, vals_alt, n, end_bit, digit_bits, stream=None) -> bool:
+    """Sort with the library's static scratch array (no allocation).
+    Returns True when the result is in the *_alt buffers."""
+    alt = c_i32(0)
+    check(load().qb_sort_pairs_noalloc(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt), n, end_bit, digit_bits,
+                                       ctypes.byref(alt), stream_handle(stream)))
     return bool(alt.value)

@@ -127,6 +127,10 @@ qb_status check_camera(const qb_frame *f, const qb_camera *c) {
 
 }  // namespace
 
+namespace qb {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace qb
+
 extern "C" {
 
 const char *qb_last_error(void) { return g_err.c_str(); }

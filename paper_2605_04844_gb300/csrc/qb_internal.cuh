@@ -49,6 +49,9 @@ struct Layout {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Sets the message qb_last_error() returns on the calling thread.
+void set_last_error(const char *msg);
+
 // ---- sort -------------------------------------------------------------------
 size_t sort_scratch_bytes(uint64_t n, int end_bit, int digit_bits);
 // Sorts pairs on bits [0, end_bit).  n_dev: device count (<= n_max) or null
