@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--digit-bits", type=int, default=None)
+    ap.add_argument("--sort-mode", default="depth_first", choices=["depth_first", "full_key"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--out", default=None, help="also write the JSON line here")
     return ap.parse_args()
@@ -134,11 +135,15 @@ def run_ours(args, rank, world, local_rank):
 
     frames, pairs = {}, {}
     for mode in ("quadbox", "aabb3s"):
-        _, fr = R.forward(sd, cam, mode, bg=bg, digit_bits=digit_bits)
+        _, fr = R.forward(sd, cam, mode, bg=bg, digit_bits=digit_bits, sort_mode=args.sort_mode)
         pairs[mode] = fr.n_pairs
         cap = int(fr.n_pairs * 1.1) + 4096
         frames[mode] = R.Frame(n, W, H, cap)
-        frames[mode].set_tuning(digit_bits=digit_bits)
+        frames[mode].set_tuning(digit_bits=digit_bits, sort_mode=args.sort_mode)
+    # the same QuadBox frame with the other pair-ordering scheme, for comparison
+    other_mode = "full_key" if args.sort_mode == "depth_first" else "depth_first"
+    frames["quadbox_other"] = R.Frame(n, W, H, int(pairs["quadbox"] * 1.1) + 4096)
+    frames["quadbox_other"].set_tuning(digit_bits=8, sort_mode=other_mode)
     img = torch.empty((3, H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     grads = {k: torch.zeros_like(sd[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
@@ -165,7 +170,8 @@ def run_ours(args, rank, world, local_rank):
             N.qb_render_bwd(fr.frame, scene_s, cam_s, bg, dL, gs, None)
             ev[5].record(stream)
 
-    mode_of = {id(frames["quadbox"]): "quadbox", id(frames["aabb3s"]): "aabb3s"}
+    mode_of = {id(frames["quadbox"]): "quadbox", id(frames["aabb3s"]): "aabb3s",
+               id(frames["quadbox_other"]): "quadbox"}
 
     def run_phase(mode, with_bwd, steps, warmup):
         fr = frames[mode]
@@ -211,6 +217,7 @@ def run_ours(args, rank, world, local_rank):
     fb_ms, fb_stages = run_phase("quadbox", True, args.steps, args.warmup)
     afwd_ms, afwd_stages = run_phase("aabb3s", False, args.steps, args.warmup)
     afb_ms, afb_stages = run_phase("aabb3s", True, args.steps, args.warmup)
+    ofwd_ms, ofwd_stages = run_phase("quadbox_other", False, args.steps, args.warmup)
     torch.cuda.synchronize()
     barrier()
     wall = time.time() - t_wall0
@@ -268,7 +275,8 @@ def run_ours(args, rank, world, local_rank):
                                "3-sigma) vs 3-sigma AABB on the same kernels",
                    "n_gaussians": n, "width": W, "height": H, "sh_degree": 3,
                    "l2": "L2 flushed (258 MB write) between timed steps; scene inputs 236 MB > L2",
-                   "sort_digit_bits": digit_bits, "parallelism": f"replicas x{world}"},
+                   "sort_digit_bits": digit_bits, "sort_mode": args.sort_mode,
+                   "parallelism": f"replicas x{world}"},
         "quadbox": {"fwd_fps": round(1000.0 / fwd_ms, 2), "fwd_ms": round(fwd_ms, 4),
                     "fwd_bwd_ms": round(fb_ms, 4), "pairs_per_frame": P,
                     "stage_ms": {k: round(v, 4) for k, v in fb_stages.items()}},
@@ -277,22 +285,50 @@ def run_ours(args, rank, world, local_rank):
                    "stage_ms": {k: round(v, 4) for k, v in afb_stages.items()}},
         "speedup_vs_aabb": {"fwd": round(afwd_ms / fwd_ms, 3), "fwd_bwd": round(afb_ms / fb_ms, 3),
                             "pair_ratio": round(pairs["aabb3s"] / max(P, 1), 3)},
+        "quadbox_" + other_mode: {"fwd_ms": round(ofwd_ms, 4),
+                                   "stage_ms": {k: round(v, 4) for k, v in ofwd_stages.items()}},
         "paper_context": "paper: 1.85x FPS over 3DGS, mean over Mip-NeRF 360/DB/T&T on NVIDIA A100 (Table 1)",
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
         "wall_s_timed": round(wall, 2),
     }
-    result["roofline"] = roofline(fwd_stages, fb_stages, P, n, W, H, digit_bits, n_eval, clk)
-    passes = -(-(31 + (((W + 15) // 16) * ((H + 15) // 16) - 1).bit_length()) // digit_bits)
-    per_fwd = 1 + 3 + 1 + 2 + passes + 1 + 1
-    result["gpu_launches"] = args.steps * (2 * per_fwd + 2 * (per_fwd + 2)) + args.steps * per_fwd
+    result["roofline"] = roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode)
+    tile_bits = (((W + 15) // 16) * ((H + 15) // 16) - 1).bit_length()
+    if args.sort_mode == "depth_first":
+        per_fwd = 1 + (1 + 2 + 4) + 3 + 1 + (2 + -(-tile_bits // digit_bits)) + 1 + 1
+        per_other = 1 + 3 + 1 + (2 + -(-(31 + tile_bits) // 8)) + 1 + 1
+    else:
+        per_fwd = 1 + 3 + 1 + (2 + -(-(31 + tile_bits) // digit_bits)) + 1 + 1
+        per_other = 1 + (1 + 2 + 4) + 3 + 1 + (2 + -(-tile_bits // 8)) + 1 + 1
+    # fwd and fwd+bwd phases for both binnings, the comparison phase, the e2e loop
+    result["gpu_launches"] = args.steps * (2 * per_fwd + 2 * (per_fwd + 2) + per_other + per_fwd)
     if tune:
         result["autotune"] = tune
     return result
 
 
-def roofline(fwd_stages, fb_stages, P, n, W, H, digit_bits, n_eval, clk):
+def stage_bytes(P, n, W, H, digit_bits, sort_mode):
+    """Algorithmic HBM bytes of the emit and sort stages of one frame."""
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    tile_bits = (tiles - 1).bit_length()
+    if sort_mode == "depth_first":
+        # tile sort: upfront histogram reads 4 B keys; each pass reads and
+        # writes 4 B key + 4 B value; ranges read 4 B keys
+        passes = -(-tile_bits // digit_bits)
+        sort_bytes = P * (4 + passes * 16 + 4) + tiles * 8
+        # emit: depth keys (read 20 B, write 8 B per Gaussian), depth sort of n
+        # 4-byte keys + values (4 passes), scan (read 8 B, write 4 B), box record
+        # read (48 B), pairs written (8 B each)
+        emit_bytes = n * (28 + 4 * 16 + 4 + 12 + 48) + 8 * P
+    else:
+        passes = -(-(31 + tile_bits) // digit_bits)
+        sort_bytes = P * (8 + passes * 24 + 8) + tiles * 8
+        emit_bytes = n * (12 + 48) + 12 * P
+    return sort_bytes, emit_bytes
+
+
+def roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
     """Roofline of the dominant kernel of the forward step (see the design doc for
     the algorithmic bytes and flops per unit)."""
     peaks = {}
@@ -301,10 +337,7 @@ def roofline(fwd_stages, fb_stages, P, n, W, H, digit_bits, n_eval, clk):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    tiles = ((W + 15) // 16) * ((H + 15) // 16)
-    key_bits = 31 + (tiles - 1).bit_length()
-    passes = -(-key_bits // digit_bits)
-    sort_bytes = P * (8 + passes * 24 + 8) + tiles * 8
+    sort_bytes, emit_bytes = stage_bytes(P, n, W, H, digit_bits, sort_mode)
     dom = max(fwd_stages, key=lambda k: fwd_stages[k])
     out = {}
     if dom == "render" and n_eval:
@@ -322,7 +355,6 @@ def roofline(fwd_stages, fb_stages, P, n, W, H, digit_bits, n_eval, clk):
                "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     # secondary: the HBM-bound stages
-    emit_bytes = 12 * P + 44 * n
     out["hbm_stages"] = {
         "sort": {"GB/s": round(sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9, 1),
                  "frac": round(sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9 / hbm, 4), "bytes": sort_bytes},

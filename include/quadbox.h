@@ -69,6 +69,15 @@ typedef enum {
 } qb_bin_mode;
 #define QB_BIN_NO_CLAMP 0x100
 
+/* How qb_bin_emit/qb_sort order the pairs by (tile, depth, index).  Both give
+ * identical sorted values and ranges.
+ *  DEPTH_FIRST  (default) sort the n Gaussians by (depth, index) once, emit
+ *               each Gaussian's pairs in that order with 32-bit tile keys, then
+ *               stable-sort the pairs on the tile bits only.
+ *  FULL_KEY     emit in index order with 64-bit keys (tile << 31) | depth
+ *               bits and stable-sort on all 31 + tile bits (SortPairs, Sec. 2). */
+typedef enum { QB_SORT_DEPTH_FIRST = 0, QB_SORT_FULL_KEY = 1 } qb_sort_mode;
+
 /* Pinhole camera.  viewmat: row-major 4x4 world->view, last row (0,0,0,1);
  * view space looks down +z.  Pixel (px, py) has its centre at
  * (px, py) = (fx x/z + cx, fy y/z + cy); normally cx = (width-1)/2.
@@ -130,7 +139,9 @@ typedef struct {
     int32_t sort_digit_bits;  /* 8..11, radix digit width of qb_sort        */
     int32_t render_batch;     /* Gaussians staged per shared-memory batch   */
     int32_t sorted_in_alt;    /* internal: sorted pairs live in buffer 1    */
-    int32_t reserved[5];
+    int32_t sort_mode;        /* qb_sort_mode; set before qb_bin_emit       */
+    int32_t depth_in_alt;     /* internal: depth order lives in buffer 1    */
+    int32_t reserved[3];
 } qb_frame;
 
 /* Device arrays inside a frame workspace (for inspection and tests).  All
@@ -144,9 +155,12 @@ typedef struct {
     int32_t *meta;      /* [n]     bit0 visible, bit1 orient (Sigma12 >= 0),
                                    bits2-4 colour channel clamped at 0      */
     uint32_t *counts;   /* [n]     tiles per Gaussian                       */
-    uint32_t *offsets;  /* [n]     exclusive prefix of counts               */
-    uint64_t *keys;     /* [P]     (tile << 31) | depth bits, sorted after qb_sort */
+    uint32_t *offsets;  /* [n]     exclusive prefix of counts in emission order
+                                   (index order, or depth order in DEPTH_FIRST) */
+    uint64_t *keys;     /* [P]     FULL_KEY: (tile << 31) | depth bits, sorted after qb_sort */
+    uint32_t *tile_keys;/* [P]     DEPTH_FIRST: tile id, sorted after qb_sort */
     uint32_t *vals;     /* [P]     Gaussian index                           */
+    uint32_t *depth_order; /* [n]  DEPTH_FIRST: Gaussians by (depth, index) */
     uint32_t *ranges;   /* [tiles][2] [start, end) into keys/vals           */
     float *t_final;     /* [H][W]  transmittance after the last contributor */
     int32_t *n_contrib; /* [H][W]  1 + position of the last contributor     */
@@ -193,17 +207,18 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
 
 /* Stage 2 (Sec. 2 "DuplicateWithKeys", Sec. 3.2 QPass): exclusive scan of the
  * tile counts, then one (key, value) pair per Gaussian-tile overlap with
- * key = (tile << 31) | float bits of the depth, value = Gaussian index,
- * written at the Gaussian's scan offset (so pairs appear in Gaussian order).
+ * key = (tile << 31) | float bits of the depth (FULL_KEY) or the tile id
+ * (DEPTH_FIRST, after sorting the Gaussians by depth), value = Gaussian
+ * index, written at the Gaussian's scan offset in emission order.
  * If n_pairs_out is non-NULL the host synchronises once to read P, stores it
  * in *n_pairs_out and frame->n_pairs, and returns CAPACITY (writing no pairs)
  * when P > pair_capacity.  With NULL nothing synchronises; an overflow is
  * then flagged on the device and reported by qb_frame_check. */
 qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream);
 
-/* Stage 3 (Sec. 2 "SortPairs"): stable LSD radix sort of the pairs on the
- * key bits [0, 31 + tile bits) with the library's onesweep sort, then the
- * per-tile [start, end) ranges. */
+/* Stage 3 (Sec. 2 "SortPairs"): stable LSD radix sort of the pairs with the
+ * library's onesweep sort on the key bits [0, 31 + tile bits) (FULL_KEY) or
+ * [0, tile bits) (DEPTH_FIRST), then the per-tile [start, end) ranges. */
 qb_status qb_sort(qb_frame *frame, qb_stream_t stream);
 
 /* Stage 4 (Sec. 2 "Render", Eq. 2): front-to-back compositing per pixel.
@@ -218,10 +233,12 @@ qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_strea
  * sum(d_dL_dimg * image) w.r.t. the scene parameters.  scene, camera and bg
  * must be those of the forward pass.  d_dL_dimg: device float [3][H][W].
  * If d_grad_screen is non-NULL it receives the screen-space gradients,
- * float [n][9] = (d mu_x, d mu_y, d a, d b, d c, d o, d r, d g, d b),
- * and must be zeroed by the caller. */
+ * double [n][9] = dL/d(mu_x, mu_y, Sigma11, Sigma12, Sigma22, o, r, g, b),
+ * Sigma the 2D covariance with Sigma12 counted once (the conic gradient is
+ * dL/dLambda = -Sigma dL/dSigma Sigma), and must be zeroed by the caller;
+ * the sums over pixels are accumulated in float64. */
 qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, const float *bg,
-                        const float *d_dL_dimg, qb_scene_grads *grads, float *d_grad_screen,
+                        const float *d_dL_dimg, qb_scene_grads *grads, double *d_grad_screen,
                         qb_stream_t stream);
 
 /* Standalone pair sort (the sort used by qb_sort): sorts n (key, value)

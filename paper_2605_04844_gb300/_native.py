@@ -21,6 +21,7 @@ c_size = ctypes.c_size_t
 QB_OK, QB_ERR_INVALID_ARG, QB_ERR_CUDA, QB_ERR_CAPACITY, QB_ERR_TIMEOUT, QB_ERR_STATE = range(6)
 QB_BIN_AABB3S, QB_BIN_QUADBOX, QB_BIN_ADR, QB_BIN_QUADBOX_NAIVE, QB_BIN_DUALBOX = range(5)
 QB_BIN_NO_CLAMP = 0x100
+QB_SORT_DEPTH_FIRST, QB_SORT_FULL_KEY = 0, 1
 MODE_NAMES = {"aabb3s": 0, "quadbox": 1, "adr": 2, "quadbox_naive": 3, "dualbox": 4}
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "CAPACITY", 4: "TIMEOUT", 5: "STATE"}
 
@@ -55,13 +56,13 @@ class QbFrame(ctypes.Structure):
                 ("pair_capacity", c_u64), ("workspace", c_vp), ("workspace_bytes", c_size),
                 ("bin_mode", c_i32), ("sh_degree", c_i32), ("key_bits", c_i32), ("stage", c_i32),
                 ("n_pairs", c_u64), ("sort_digit_bits", c_i32), ("render_batch", c_i32),
-                ("sorted_in_alt", c_i32), ("reserved", c_i32 * 5)]
+                ("sorted_in_alt", c_i32), ("sort_mode", c_i32), ("depth_in_alt", c_i32), ("reserved", c_i32 * 3)]
 
 
 class QbFrameArrays(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("xy", "conic_o", "rgbd", "box", "r3", "meta", "counts", "offsets",
-                                          "keys", "vals", "ranges", "t_final", "n_contrib", "n_eval", "n_pairs",
-                                          "err_flags")]
+                                          "keys", "tile_keys", "vals", "depth_order", "ranges", "t_final",
+                                          "n_contrib", "n_eval", "n_pairs", "err_flags")]
 
 
 _lib = None

@@ -66,11 +66,21 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     }
     L.sort_scratch_bytes = sb;
     L.sort_scratch = take(sb);
+    L.dkeys0 = take(4 * N);
+    L.dkeys1 = take(4 * N);
+    L.dvals0 = take(4 * N);
+    L.dvals1 = take(4 * N);
+    size_t db = 0;
+    for (int d = 8; d <= kMaxDigitBits; ++d) {
+        size_t b = sort_scratch_bytes(N, kDepthBits, d);
+        if (b > db) db = b;
+    }
+    L.dsort_scratch = take(db);
     L.ranges = take(8 * (size_t)tiles);
     L.tfinal = take(4 * (size_t)W * H);
     L.ncontrib = take(4 * (size_t)W * H);
     L.neval = take(4 * (size_t)W * H);
-    L.gscreen = take(36 * N);
+    L.gscreen = take(72 * N);
     L.state = take(256);
     L.total = off;
     return true;
@@ -168,6 +178,7 @@ qb_status qb_frame_init(qb_frame *frame, int32_t n, int32_t width, int32_t heigh
     frame->n_pairs = UINT64_MAX;
     frame->sort_digit_bits = 8;
     frame->render_batch = 256;
+    frame->sort_mode = QB_SORT_DEPTH_FIRST;
     QB_CUDA(cudaMemsetAsync(at<uint8_t>(frame, L.state), 0, 256, (cudaStream_t)stream));
     return QB_OK;
 }
@@ -187,7 +198,9 @@ qb_status qb_frame_arrays_get(const qb_frame *frame, qb_frame_arrays *out) {
     out->counts = at<uint32_t>(frame, L.counts);
     out->offsets = at<uint32_t>(frame, L.offsets);
     out->keys = at<uint64_t>(frame, alt ? L.keys1 : L.keys0);
+    out->tile_keys = at<uint32_t>(frame, alt ? L.keys1 : L.keys0);
     out->vals = at<uint32_t>(frame, alt ? L.vals1 : L.vals0);
+    out->depth_order = at<uint32_t>(frame, frame->depth_in_alt ? L.dvals1 : L.dvals0);
     out->ranges = at<uint32_t>(frame, L.ranges);
     out->t_final = at<float>(frame, L.tfinal);
     out->n_contrib = at<int32_t>(frame, L.ncontrib);
@@ -252,9 +265,26 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     qb_status st = check_frame(frame, L);
     if (st != QB_OK) return st;
     if (frame->stage < 1) return fail(QB_ERR_STATE, "qb_bin_emit before qb_preprocess");
+    if (frame->sort_mode != QB_SORT_DEPTH_FIRST && frame->sort_mode != QB_SORT_FULL_KEY)
+        return fail(QB_ERR_INVALID_ARG, "sort_mode must be QB_SORT_DEPTH_FIRST or QB_SORT_FULL_KEY");
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t *d_np = at<uint64_t>(frame, L.state);
-    QB_CUDA(launch_scan(at<uint32_t>(frame, L.counts), frame->n, at<uint32_t>(frame, L.offsets),
+    uint32_t *err = at<uint32_t>(frame, L.state + 8);
+    const bool depth_first = frame->sort_mode == QB_SORT_DEPTH_FIRST;
+    const uint32_t *perm = nullptr;
+    if (depth_first) {
+        // emission order = Gaussians sorted by (depth, index)
+        uint32_t *dk0 = at<uint32_t>(frame, L.dkeys0), *dk1 = at<uint32_t>(frame, L.dkeys1);
+        uint32_t *dv0 = at<uint32_t>(frame, L.dvals0), *dv1 = at<uint32_t>(frame, L.dvals1);
+        QB_CUDA(launch_depth_keys(frame->n, at<float4>(frame, L.rgbd), at<uint32_t>(frame, L.counts), dk0, dv0, s));
+        int passes = 0;
+        if (frame->n > 0)
+            QB_CUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)frame->n, nullptr, kDepthBits, 8,
+                               at<void>(frame, L.dsort_scratch), err, s, &passes));
+        frame->depth_in_alt = passes & 1;
+        perm = frame->depth_in_alt ? dv1 : dv0;
+    }
+    QB_CUDA(launch_scan(at<uint32_t>(frame, L.counts), perm, frame->n, at<uint32_t>(frame, L.offsets),
                         at<uint64_t>(frame, L.scan_part), d_np, s));
     frame->n_pairs = UINT64_MAX;
     if (n_pairs_out) {
@@ -271,6 +301,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     }
     EmitArgs a;
     a.n = frame->n;
+    a.perm = perm;
     a.xy = at<float2>(frame, L.xy);
     a.box = at<float4>(frame, L.box);
     a.r3 = at<float>(frame, L.r3);
@@ -278,7 +309,6 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     a.rgbd = at<float4>(frame, L.rgbd);
     a.counts = at<uint32_t>(frame, L.counts);
     a.offsets = at<uint32_t>(frame, L.offsets);
-    a.keys = at<uint64_t>(frame, L.keys0);
     a.vals = at<uint32_t>(frame, L.vals0);
     a.n_pairs = d_np;
     a.capacity = frame->pair_capacity;
@@ -287,8 +317,11 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     a.W = frame->width;
     a.H = frame->height;
     a.tiles_x = frame->tiles_x;
-    a.err = at<uint32_t>(frame, L.state + 8);
-    QB_CUDA(launch_emit(a, s));
+    a.err = err;
+    if (depth_first)
+        QB_CUDA(launch_emit<uint32_t>(a, at<uint32_t>(frame, L.keys0), s));
+    else
+        QB_CUDA(launch_emit<uint64_t>(a, at<uint64_t>(frame, L.keys0), s));
     frame->stage = 2;
     return QB_OK;
 }
@@ -305,12 +338,26 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
     const uint64_t n_max = known ? frame->n_pairs : frame->pair_capacity;
     const uint64_t *n_dev = known ? nullptr : at<uint64_t>(frame, L.state);
     int passes = 0;
-    QB_CUDA(sort_pairs(at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint64_t>(frame, L.keys1),
-                       at<uint32_t>(frame, L.vals1), n_max, n_dev, frame->key_bits, frame->sort_digit_bits,
-                       at<void>(frame, L.sort_scratch), at<uint32_t>(frame, L.state + 8), s, &passes));
-    frame->sorted_in_alt = passes & 1;
-    const uint64_t *sorted = at<uint64_t>(frame, frame->sorted_in_alt ? L.keys1 : L.keys0);
-    QB_CUDA(launch_ranges(sorted, n_max, n_dev, at<uint2>(frame, L.ranges), frame->tiles_x * frame->tiles_y, s));
+    const int ntiles = frame->tiles_x * frame->tiles_y;
+    uint32_t *err = at<uint32_t>(frame, L.state + 8);
+    if (frame->sort_mode == QB_SORT_DEPTH_FIRST) {
+        // pairs were emitted in depth order: a stable sort on the tile id alone
+        const int tile_bits = frame->key_bits - kDepthBits;
+        if (tile_bits > 0)
+            QB_CUDA(sort_pairs(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
+                               at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1), n_max, n_dev, tile_bits,
+                               frame->sort_digit_bits, at<void>(frame, L.sort_scratch), err, s, &passes));
+        frame->sorted_in_alt = passes & 1;
+        const uint32_t *sorted = at<uint32_t>(frame, frame->sorted_in_alt ? L.keys1 : L.keys0);
+        QB_CUDA(launch_ranges<uint32_t>(sorted, n_max, n_dev, at<uint2>(frame, L.ranges), ntiles, s));
+    } else {
+        QB_CUDA(sort_pairs(at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint64_t>(frame, L.keys1),
+                           at<uint32_t>(frame, L.vals1), n_max, n_dev, frame->key_bits, frame->sort_digit_bits,
+                           at<void>(frame, L.sort_scratch), err, s, &passes));
+        frame->sorted_in_alt = passes & 1;
+        const uint64_t *sorted = at<uint64_t>(frame, frame->sorted_in_alt ? L.keys1 : L.keys0);
+        QB_CUDA(launch_ranges<uint64_t>(sorted, n_max, n_dev, at<uint2>(frame, L.ranges), ntiles, s));
+    }
     frame->stage = 3;
     return QB_OK;
 }
@@ -342,7 +389,7 @@ qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_strea
 }
 
 qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, const float *bg,
-                        const float *d_dL_dimg, qb_scene_grads *grads, float *d_grad_screen, qb_stream_t stream) {
+                        const float *d_dL_dimg, qb_scene_grads *grads, double *d_grad_screen, qb_stream_t stream) {
     Layout L;
     qb_status st = check_frame(frame, L);
     if (st != QB_OK) return st;
@@ -354,10 +401,10 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
     if (frame->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
         return fail(QB_ERR_INVALID_ARG, "a gradient array is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    float *gscreen = d_grad_screen;
+    double *gscreen = d_grad_screen;
     if (!gscreen) {
-        gscreen = at<float>(frame, L.gscreen);
-        QB_CUDA(cudaMemsetAsync(gscreen, 0, 36 * (size_t)frame->n, s));
+        gscreen = at<double>(frame, L.gscreen);
+        QB_CUDA(cudaMemsetAsync(gscreen, 0, 72 * (size_t)frame->n, s));
     }
     BwdArgs b;
     b.ranges = at<uint2>(frame, L.ranges);

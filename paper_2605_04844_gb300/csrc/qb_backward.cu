@@ -11,10 +11,12 @@
 //   dC/dalpha_k = T_k c_k - B_k / (1 - alpha_k)
 // alpha = min(0.99, o G), G = exp(power): zero derivative where the cap binds.
 // Per Gaussian the 32 lanes of a warp are summed with shuffles and one lane
-// adds the 9 screen-space gradients atomically.
+// adds the 9 screen-space gradients atomically in float64: (mu_x, mu_y,
+// Sigma11, Sigma12, Sigma22, o, r, g, b), the covariance entries being the
+// well-conditioned parametrisation (dL/dLambda = -Sigma dL/dSigma Sigma).
 //
-// K8: one thread per Gaussian chains (mu^2D, conic, o, colour) gradients to
-// means, (log-)scales, quaternions, opacity (logits) and SH.
+// K8: one thread per Gaussian chains the (mu^2D, Sigma2D, o, colour) gradients
+// to means, (log-)scales, quaternions, opacity (logits) and SH.
 #include "qb_kernels.cuh"
 #include "qb_project.cuh"
 
@@ -102,13 +104,16 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
                         B1 = fmaf(w, c.y, B1);
                         B2 = fmaf(w, c.z, B2);
                         if (oG < kAlphaMax) {
+                            // power = -d^T Lambda d / 2 with Lambda = Sigma^-1 and u = Lambda d:
+                            // dpower/dmu = -u, dpower/dSigma = u u^T / 2
                             const float dpower = dalpha * oG;
+                            const float ux = co.x * dx + co.y * dy, uy = co.y * dx + co.z * dy;
                             gv[5] = G * dalpha;
-                            gv[2] = -0.5f * dpower * dx * dx;
-                            gv[3] = -dpower * dx * dy;
-                            gv[4] = -0.5f * dpower * dy * dy;
-                            gv[0] = dpower * (-co.x * dx - co.y * dy);
-                            gv[1] = dpower * (-co.y * dx - co.z * dy);
+                            gv[0] = -dpower * ux;
+                            gv[1] = -dpower * uy;
+                            gv[2] = 0.5f * dpower * ux * ux;
+                            gv[3] = dpower * ux * uy;
+                            gv[4] = 0.5f * dpower * uy * uy;
                         }
                     }
                 }
@@ -117,10 +122,12 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
 #pragma unroll
                 for (int v = 0; v < 9; ++v) gv[v] = warp_sum(gv[v]);
                 if (lane == 0) {
-                    float *dst = a.g_screen + (size_t)s_id[j] * 9;
+                    // float64 accumulation across warps and tiles: a large Gaussian
+                    // sums thousands of terms of both signs
+                    double *dst = a.g_screen + (size_t)s_id[j] * 9;
 #pragma unroll
                     for (int v = 0; v < 9; ++v)
-                        if (gv[v] != 0.f) atomicAdd(dst + v, gv[v]);
+                        if (gv[v] != 0.f) atomicAdd(dst + v, (double)gv[v]);
                 }
             }
         }
@@ -146,17 +153,12 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PreBwdArgs a) {
     if (!project_gaussian(cam, m0, m1, m2, a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2],
                           a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3], a.raw, p))
         return;
-    const float *gsc = a.g_screen + (size_t)i * 9;
-    const float gmx = gsc[0], gmy = gsc[1], ga = gsc[2], gb = gsc[3], gc = gsc[4], gop = gsc[5];
-    const float grgb[3] = {gsc[6], gsc[7], gsc[8]};
-
-    // conic -> Sigma2D: H = -Lambda Ghat Lambda, Ghat = [ga gb/2; gb/2 gc]
-    const float g12 = 0.5f * gb;
-    const float t00 = p.a * ga + p.b * g12, t01 = p.a * g12 + p.b * gc;
-    const float t10 = p.b * ga + p.c * g12, t11 = p.b * g12 + p.c * gc;
-    const float H00 = -(t00 * p.a + t01 * p.b);
-    const float H01 = -0.5f * ((t00 * p.b + t01 * p.c) + (t10 * p.a + t11 * p.b));
-    const float H11 = -(t10 * p.b + t11 * p.c);
+    const double *gsc = a.g_screen + (size_t)i * 9;
+    const float gmx = (float)gsc[0], gmy = (float)gsc[1], gop = (float)gsc[5];
+    const float grgb[3] = {(float)gsc[6], (float)gsc[7], (float)gsc[8]};
+    // gradient w.r.t. Sigma2D = [s11 s12; s12 s22] (s12 one parameter) as the
+    // full-matrix gradient H with dL = tr(H^T dSigma)
+    const float H00 = (float)gsc[2], H01 = 0.5f * (float)gsc[3], H11 = (float)gsc[4];
     // Sigma2D = A A^T + 0.3 I  ->  dL/dA = 2 H A
     float gA[6];
 #pragma unroll

@@ -41,6 +41,7 @@ struct Layout {
     size_t scan_part;
     size_t keys0, keys1, vals0, vals1;
     size_t sort_scratch, sort_scratch_bytes;
+    size_t dkeys0, dkeys1, dvals0, dvals1, dsort_scratch;  // depth order of the Gaussians
     size_t ranges, tfinal, ncontrib, neval;
     size_t gscreen;  // [n][9] screen-space gradients
     size_t state;  // u64 n_pairs, u32 err_flags, padding
@@ -58,6 +59,10 @@ size_t sort_scratch_bytes(uint64_t n, int end_bit, int digit_bits);
 // when n_max is exact.  Returns the number of passes; result lies in the alt
 // buffers when the pass count is odd.
 cudaError_t sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                       uint64_t n_max, const uint64_t *n_dev, int end_bit, int digit_bits,
+                       void *scratch, uint32_t *err_flags, cudaStream_t stream, int *passes_out);
+// The same sort on 32-bit keys (end_bit <= 32).
+cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                        uint64_t n_max, const uint64_t *n_dev, int end_bit, int digit_bits,
                        void *scratch, uint32_t *err_flags, cudaStream_t stream, int *passes_out);
 
@@ -180,6 +185,36 @@ __device__ __forceinline__ void qpass_line(const QPass &qp, int s, int &lo, int 
         lo = hit ? min(lo, o0) : lo;
         hi = hit ? max(hi, o1) : hi;
     }
+}
+
+// Runs of consecutive scan lines whose merged interval is the same: the
+// interval of a line changes only where a sub-box's range on the scan axis
+// begins or ends, so the QPass output is a union of at most 7 disjoint
+// rectangles ("segments"), each visited line by line exactly as QPass does.
+struct QSeg {
+    int s0, lo;   // first line, first tile on the other axis
+    int nl, len;  // lines in the run, interval length
+};
+
+__device__ __forceinline__ int qpass_segments(const QPass &qp, QSeg seg[7]) {
+    int ns = 0;
+    int cur = qp.s0;
+    while (cur <= qp.s1 && ns < 7) {
+        int next = qp.s1 + 1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const Rect &r = qp.b[q];
+            if (rect_empty(r)) continue;
+            const int a0 = qp.columns ? r.x0 : r.y0, a1 = qp.columns ? r.x1 : r.y1;
+            if (a0 > cur) next = min(next, a0);
+            if (a1 + 1 > cur) next = min(next, a1 + 1);
+        }
+        int lo, hi;
+        qpass_line(qp, cur, lo, hi);
+        if (hi >= lo) seg[ns++] = QSeg{cur, lo, next - cur, hi - lo + 1};
+        cur = next;
+    }
+    return ns;
 }
 
 __device__ __forceinline__ uint32_t qpass_count(const Rect rects[4]) {

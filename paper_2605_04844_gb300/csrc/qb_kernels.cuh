@@ -21,13 +21,14 @@ struct PreArgs {
 
 struct EmitArgs {
     int n;
+    const uint32_t *perm;  // emission order -> Gaussian (null: index order)
     const float2 *xy;
     const float4 *box;
     const float *r3;
     const int *meta;
     const float4 *rgbd;
-    const uint32_t *counts, *offsets;
-    uint64_t *keys;
+    const uint32_t *counts;   // by Gaussian
+    const uint32_t *offsets;  // by emission position
     uint32_t *vals;
     const uint64_t *n_pairs;
     uint64_t capacity;
@@ -60,7 +61,7 @@ struct BwdArgs {
     const float *dL_dimg;  // [3][H][W]
     const float *tfinal;
     const int *ncontrib;
-    float *g_screen;  // [n][9]: mu_x, mu_y, a, b, c, o, r, g, b
+    double *g_screen;  // [n][9]: mu_x, mu_y, Sigma11, Sigma12, Sigma22, o, r, g, b
 };
 
 struct PreBwdArgs {
@@ -69,16 +70,20 @@ struct PreBwdArgs {
     bool raw;
     CamDev cam;
     const int *meta;
-    const float *g_screen;  // [n][9]
+    const double *g_screen;  // [n][9]
     float *gm, *gs, *gq, *go, *gsh;
 };
 
 cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s);
-cudaError_t launch_scan(const uint32_t *counts, int n, uint32_t *offsets, uint64_t *partials, uint64_t *n_pairs,
-                        cudaStream_t s);
+cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uint32_t *offsets, uint64_t *partials,
+                        uint64_t *n_pairs, cudaStream_t s);
 size_t scan_partials_count(int n);
-cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);
-cudaError_t launch_ranges(const uint64_t *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges, int ntiles,
+cudaError_t launch_depth_keys(int n, const float4 *rgbd, const uint32_t *counts, uint32_t *keys, uint32_t *vals,
+                              cudaStream_t s);
+template <typename KeyT>
+cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s);
+template <typename KeyT>
+cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges, int ntiles,
                           cudaStream_t s);
 cudaError_t launch_render(const RenderArgs &a, int batch, cudaStream_t s);
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s);

@@ -57,13 +57,17 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
 
     Rect rects[4];
     box_rects(p.mx, p.my, bt.box, bt.r3, bt.orient, a.mode, a.clamp3s, cam.W, cam.H, rects);
-    uint32_t cnt;
-    if (a.mode == QB_BIN_AABB3S || a.mode == QB_BIN_ADR) {
-        cnt = rect_empty(rects[0]) ? 0u : (uint32_t)((rects[0].x1 - rects[0].x0 + 1) * (rects[0].y1 - rects[0].y0 + 1));
-    } else if (a.mode == QB_BIN_QUADBOX_NAIVE) {
+    uint32_t cnt = 0;
+    if (a.mode == QB_BIN_QUADBOX_NAIVE) {
         cnt = naive_count(rects);
     } else {
-        cnt = qpass_count(rects);
+        // QPass count: the lines of each run of equal intervals times its length
+        QPass qp;
+        if (qpass_setup(rects, qp)) {
+            QSeg seg[7];
+            const int ns = qpass_segments(qp, seg);
+            for (int q = 0; q < ns; ++q) cnt += (uint32_t)(seg[q].nl * seg[q].len);
+        }
     }
 
     a.xy[i] = make_float2(p.mx, p.my);

@@ -83,8 +83,8 @@ size_t sort_scratch_bytes(uint64_t n, int end_bit, int digit_bits) {
 }
 
 // Upfront histogram of every pass's digit.
-template <int RB>
-__global__ void __launch_bounds__(256) sort_hist_kernel(const uint64_t *__restrict__ keys, uint64_t n_max,
+template <int RB, typename KeyT>
+__global__ void __launch_bounds__(256) sort_hist_kernel(const KeyT *__restrict__ keys, uint64_t n_max,
                                                         const uint64_t *n_dev, int passes, uint32_t *hist) {
     constexpr int R = 1 << RB;
     extern __shared__ uint32_t sh[];
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const uint64_t *__restri
     const uint64_t n = n_dev ? min(*n_dev, n_max) : n_max;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[idx];
+        const KeyT k = keys[idx];
         for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * R + (int)((k >> (p * RB)) & (R - 1))], 1u);
     }
     __syncthreads();
@@ -126,15 +126,15 @@ __global__ void __launch_bounds__(1024) sort_hist_scan_kernel(uint32_t *hist) {
     }
 }
 
-template <int RB>
+template <int RB, typename KeyT>
 constexpr size_t onesweep_smem() {
-    return (size_t)kSortTile * 8 + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)2 * (1 << RB) * 4;
+    return (size_t)kSortTile * sizeof(KeyT) + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)2 * (1 << RB) * 4;
 }
 
-template <int RB>
-__global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const uint64_t *__restrict__ kin,
+template <int RB, typename KeyT>
+__global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__restrict__ kin,
                                                               const uint32_t *__restrict__ vin,
-                                                              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                              KeyT *__restrict__ kout, uint32_t *__restrict__ vout,
                                                               uint64_t n_max, const uint64_t *n_dev,
                                                               const uint32_t *__restrict__ bin_off,
                                                               uint32_t *lookback, uint32_t *counter, int shift,
@@ -143,9 +143,9 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const uint64_t *__
     constexpr uint32_t MASK = R - 1;
     constexpr int PER = (R + kSortBlock - 1) / kSortBlock;
     extern __shared__ __align__(16) uint8_t smem[];
-    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
+    KeyT *s_keys = reinterpret_cast<KeyT *>(smem);
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem);
-    uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem + (size_t)kSortTile * 8);
+    uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem + (size_t)kSortTile * sizeof(KeyT));
     uint32_t *s_gbase = reinterpret_cast<uint32_t *>(s_whist + kSortWarps * R);
     uint32_t *s_lstart = s_gbase + R;
     __shared__ uint32_t s_tile;
@@ -161,13 +161,13 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const uint64_t *__
 
     // ---- load (warp-striped: item k of lane l at wbase + 32k + l) ----
     const uint64_t wbase = tbase + (uint64_t)wid * (32 * kSortItems);
-    uint64_t key[kSortItems];
+    KeyT key[kSortItems];
     uint32_t val[kSortItems];
     uint32_t rank[kSortItems];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         uint64_t idx = wbase + 32 * k + lane;
-        key[k] = idx < n ? __ldcs(kin + idx) : ~0ull;
+        key[k] = idx < n ? __ldcs(kin + idx) : ~KeyT(0);
     }
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const uint64_t *__
     for (int k = 0; k < kSortItems; ++k) {
         uint32_t j = tid + k * kSortBlock;
         if (j < tcount) {
-            uint64_t kk = s_keys[j];
+            const KeyT kk = s_keys[j];
             uint32_t d = (uint32_t)(kk >> shift) & MASK;
             dest[k] = s_gbase[d] + (j - s_lstart[d]);
             if (dest[k] < n) kout[dest[k]] = kk;  // only false after a look-back timeout
@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const uint64_t *__
     }
 }
 
-template <int RB>
-static cudaError_t sort_impl(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n_max,
+template <int RB, typename KeyT>
+static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, uint64_t n_max,
                              const uint64_t *n_dev, int end_bit, void *scratch, uint32_t *err, cudaStream_t s,
                              int *passes_out) {
     constexpr int R = 1 << RB;
@@ -312,21 +312,22 @@ static cudaError_t sort_impl(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
 
     static bool attrs_set = false;
     if (!attrs_set) {
-        e = cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)onesweep_smem<RB>());
+        e = cudaFuncSetAttribute(onesweep_kernel<RB, KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem<RB, KeyT>());
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(sort_hist_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sort_hist_kernel<RB, KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kMaxPasses * R * 4);
         if (e != cudaSuccess) return e;
         attrs_set = true;
     }
     uint64_t hblocks = std::min<uint64_t>((n_max + 255) / 256, 152 * 4);
-    sort_hist_kernel<RB><<<(unsigned)hblocks, 256, (size_t)passes * R * 4, s>>>(keys, n_max, n_dev, passes, hist);
+    sort_hist_kernel<RB, KeyT><<<(unsigned)hblocks, 256, (size_t)passes * R * 4, s>>>(keys, n_max, n_dev, passes,
+                                                                                        hist);
     sort_hist_scan_kernel<RB><<<passes, 1024, 0, s>>>(hist);
-    uint64_t *kin = keys, *kout = keys_alt;
+    KeyT *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     for (int p = 0; p < passes; ++p) {
-        onesweep_kernel<RB><<<(unsigned)tiles, kSortBlock, onesweep_smem<RB>(), s>>>(
+        onesweep_kernel<RB, KeyT><<<(unsigned)tiles, kSortBlock, onesweep_smem<RB, KeyT>(), s>>>(
             kin, vin, kout, vout, n_max, n_dev, hist + p * kHistStride, lookback + (size_t)p * tiles * R,
             counters + p, p * RB, err);
         std::swap(kin, kout);
@@ -335,9 +336,11 @@ static cudaError_t sort_impl(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     return cudaGetLastError();
 }
 
-cudaError_t sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n_max,
-                       const uint64_t *n_dev, int end_bit, int digit_bits, void *scratch, uint32_t *err,
-                       cudaStream_t s, int *passes_out) {
+template <typename KeyT>
+static cudaError_t sort_dispatch(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, uint64_t n_max,
+                                 const uint64_t *n_dev, int end_bit, int digit_bits, void *scratch, uint32_t *err,
+                                 cudaStream_t s, int *passes_out) {
+    if (end_bit > (int)(8 * sizeof(KeyT))) return cudaErrorInvalidValue;
     switch (digit_bits) {
     case 8: return sort_impl<8>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out);
     case 9: return sort_impl<9>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out);
@@ -345,6 +348,20 @@ cudaError_t sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint3
     case 11: return sort_impl<11>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n_max,
+                       const uint64_t *n_dev, int end_bit, int digit_bits, void *scratch, uint32_t *err,
+                       cudaStream_t s, int *passes_out) {
+    return sort_dispatch(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, digit_bits, scratch, err, s,
+                         passes_out);
+}
+
+cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t n_max,
+                       const uint64_t *n_dev, int end_bit, int digit_bits, void *scratch, uint32_t *err,
+                       cudaStream_t s, int *passes_out) {
+    return sort_dispatch(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, digit_bits, scratch, err, s,
+                         passes_out);
 }
 
 }  // namespace qb

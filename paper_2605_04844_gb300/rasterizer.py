@@ -83,9 +83,11 @@ class Frame:
         N.qb_frame_init(self.frame, self.n, self.width, self.height, self.pair_capacity, self.ws, stream)
 
     # -- configuration ------------------------------------------------------
-    def set_tuning(self, digit_bits=None, render_batch=None):
+    def set_tuning(self, digit_bits=None, render_batch=None, sort_mode=None):
         if digit_bits is not None:
             self.frame.sort_digit_bits = int(digit_bits)
+        if sort_mode is not None:
+            self.frame.sort_mode = {"depth_first": 0, "full_key": 1}.get(sort_mode, sort_mode)
         if render_batch is not None:
             self.frame.render_batch = int(render_batch)
 
@@ -134,7 +136,9 @@ class Frame:
             "counts": self._view(a.counts, torch.int32, (n,)),
             "offsets": self._view(a.offsets, torch.int32, (n,)),
             "keys": self._view(a.keys, torch.int64, (P,)),
+            "tile_keys": self._view(a.tile_keys, torch.int32, (P,)),
             "vals": self._view(a.vals, torch.int32, (P,)),
+            "depth_order": self._view(a.depth_order, torch.int32, (n,)),
             "ranges": self._view(a.ranges, torch.int32, (tiles, 2)),
             "t_final": self._view(a.t_final, torch.float32, (H, W)),
             "n_contrib": self._view(a.n_contrib, torch.int32, (H, W)),
@@ -148,7 +152,8 @@ def estimate_capacity(n, width, height):
     return int(min(2 ** 30, max(1 << 16, 8 * n, 4 * tiles)))
 
 
-def forward(scene, cam, mode="quadbox", bg=None, frame: Frame | None = None, digit_bits=8, capacity=None):
+def forward(scene, cam, mode="quadbox", bg=None, frame: Frame | None = None, digit_bits=8, capacity=None,
+            sort_mode="depth_first"):
     """Full forward pass.  Returns (image [3,H,W], frame).  Grows the pair
     buffer when the tile pairs exceed it (the count is read back once)."""
     scene_s = scene_struct(scene)
@@ -156,7 +161,7 @@ def forward(scene, cam, mode="quadbox", bg=None, frame: Frame | None = None, dig
     n, W, H = scene_s.n, cam_s.width, cam_s.height
     if frame is None or frame.n != n or frame.width != W or frame.height != H:
         frame = Frame(n, W, H, capacity or estimate_capacity(n, W, H))
-    frame.set_tuning(digit_bits=digit_bits)
+    frame.set_tuning(digit_bits=digit_bits, sort_mode=sort_mode)
     while True:
         frame.preprocess(scene_s, cam_s, mode)
         try:
@@ -165,7 +170,7 @@ def forward(scene, cam, mode="quadbox", bg=None, frame: Frame | None = None, dig
         except N.QbCapacityError:
             P = _read_pairs(frame)
             frame = Frame(n, W, H, min(2 ** 30, int(P * 1.25) + 1024))
-            frame.set_tuning(digit_bits=digit_bits)
+            frame.set_tuning(digit_bits=digit_bits, sort_mode=sort_mode)
     frame.sort()
     img = frame.render(bg)
     return img, frame

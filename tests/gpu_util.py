@@ -20,14 +20,26 @@ def f64(scene):
     return {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
 
 
-def run_forward(scene, cam, mode="quadbox", bg=None, digit_bits=8, capacity=None):
+def run_forward(scene, cam, mode="quadbox", bg=None, digit_bits=8, capacity=None, sort_mode="depth_first"):
     from paper_2605_04844_gb300 import rasterizer as R
-    img, fr = R.forward(to_device(scene), cam, mode, bg=bg, digit_bits=digit_bits, capacity=capacity)
+    img, fr = R.forward(to_device(scene), cam, mode, bg=bg, digit_bits=digit_bits, capacity=capacity,
+                        sort_mode=sort_mode)
     import torch
     torch.cuda.synchronize()
     fr.check()
     A = {k: v.cpu().numpy() for k, v in fr.arrays().items()}
+    A["full_keys"] = gpu_full_keys(A, sort_mode)
     return img.cpu().numpy(), fr, A
+
+
+def gpu_full_keys(A, sort_mode):
+    """The sorted (tile << 31) | depth-bits keys: read directly in the full-key
+    mode, rebuilt from the tile keys and each value's depth in depth-first mode."""
+    if sort_mode == "full_key":
+        return A["keys"].view(np.uint64)
+    d = A["rgbd"][:, 3].astype(np.float32).view(np.uint32).astype(np.uint64) & np.uint64(0x7FFFFFFF)
+    tiles = A["tile_keys"].view(np.uint32).astype(np.uint64)
+    return (tiles << np.uint64(31)) | d[A["vals"].view(np.uint32).astype(np.int64)]
 
 
 def oracle_keys_from_gpu_boxes(A, mode, clamp, W, H):

@@ -24,7 +24,7 @@ def gpu_grads(scene, cam, G, mode="quadbox", bg=(0.1, 0.2, 0.3)):
     gs.means, gs.scales, gs.quats = g["means"].data_ptr(), g["scales"].data_ptr(), g["quats"].data_ptr()
     gs.opacities, gs.sh = g["opacities"].data_ptr(), g["sh"].data_ptr()
     n = len(scene["opacities"])
-    screen = torch.zeros((max(n, 1), 9), dtype=torch.float32, device="cuda")
+    screen = torch.zeros((max(n, 1), 9), dtype=torch.float64, device="cuda")
     Gt = torch.from_numpy(G.astype(np.float32)).cuda()
     N.qb_render_bwd(fr.frame, R.scene_struct(sd), R.camera_struct(cam), bg, Gt, gs, screen)
     torch.cuda.synchronize()
@@ -32,6 +32,20 @@ def gpu_grads(scene, cam, G, mode="quadbox", bg=(0.1, 0.2, 0.3)):
     out = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
     out["screen"] = screen.cpu().numpy()[:n].astype(np.float64)
     return out, img.cpu().numpy()
+
+
+def screen_reference(sc64, cam, scr):
+    """The oracle's screen-space gradients in the library's layout: the conic
+    gradient Ghat mapped to the covariance, H = -Lambda Ghat Lambda."""
+    proj = O.project(sc64, cam)
+    a, b, c = proj[:, O.F_A], proj[:, O.F_B], proj[:, O.F_C]
+    ga, gb, gc = scr["conic"][:, 0], 0.5 * scr["conic"][:, 1], scr["conic"][:, 2]
+    # (Lambda Ghat Lambda) entries for symmetric 2x2 matrices
+    t00, t01 = a * ga + b * gb, a * gb + b * gc
+    t10, t11 = b * ga + c * gb, b * gb + c * gc
+    H00, H01, H11 = -(t00 * a + t01 * b), -(t00 * b + t01 * c), -(t10 * b + t11 * c)
+    return np.stack([scr["xy"][:, 0], scr["xy"][:, 1], H00, 2 * H01, H11, scr["o"],
+                     scr["rgb"][:, 0], scr["rgb"][:, 1], scr["rgb"][:, 2]], axis=1)
 
 
 def normwise(a, b):
@@ -50,8 +64,7 @@ def test_backward_matches_oracle_analytic(deg):
     sc, cam, G = problem(deg=deg)
     g, _ = gpu_grads(sc, cam, G)
     ref = O.gradients(f64(sc), cam, G, bg=(0.1, 0.2, 0.3))
-    scr = ref["screen"]
-    ref_screen = np.concatenate([scr["xy"], scr["conic"], scr["o"][:, None], scr["rgb"]], axis=1)
+    ref_screen = screen_reference(f64(sc), cam, ref["screen"])
     assert normwise(g["screen"], ref_screen) <= 1e-3
     for k in KEYS:
         assert normwise(g[k], ref[k]) <= 1e-3, (k, normwise(g[k], ref[k]))

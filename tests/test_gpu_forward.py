@@ -64,27 +64,46 @@ def test_preprocess_parity(maker):
 
 @pytest.mark.parametrize("name,mode", MODES)
 @pytest.mark.parametrize("clamp", [True, False])
-def test_keys_and_ranges_bit_exact(name, mode, clamp):
+@pytest.mark.parametrize("sort_mode", ["depth_first", "full_key"])
+def test_keys_and_ranges_bit_exact(name, mode, clamp, sort_mode):
     scene, cam = c2_small()
     W, H = cam["width"], cam["height"]
     m = name if clamp else name + "+noclamp"
-    img, fr, A = run_forward(scene, cam, m)
+    img, fr, A = run_forward(scene, cam, m, sort_mode=sort_mode)
     o = oracle_keys_from_gpu_boxes(A, mode, clamp, W, H)
     np.testing.assert_array_equal(A["counts"].astype(np.int64), o["counts"])
     P = fr.n_pairs
     assert P == len(o["keys"])
-    np.testing.assert_array_equal(A["keys"].view(np.uint64), o["keys"])
+    np.testing.assert_array_equal(A["full_keys"], o["keys"])
     np.testing.assert_array_equal(A["vals"].astype(np.uint32), o["vals"])
     np.testing.assert_array_equal(A["ranges"].astype(np.int64), o["ranges"])
 
 
 @pytest.mark.parametrize("digit_bits", [8, 9, 10, 11])
-def test_keys_bit_exact_all_digit_widths(digit_bits):
+@pytest.mark.parametrize("sort_mode", ["depth_first", "full_key"])
+def test_keys_bit_exact_all_digit_widths(digit_bits, sort_mode):
     scene, cam = c1_small()
-    img, fr, A = run_forward(scene, cam, "quadbox", digit_bits=digit_bits)
+    img, fr, A = run_forward(scene, cam, "quadbox", digit_bits=digit_bits, sort_mode=sort_mode)
     o = oracle_keys_from_gpu_boxes(A, O.QUADBOX, True, cam["width"], cam["height"])
-    np.testing.assert_array_equal(A["keys"].view(np.uint64), o["keys"])
+    np.testing.assert_array_equal(A["full_keys"], o["keys"])
     np.testing.assert_array_equal(A["vals"].astype(np.uint32), o["vals"])
+
+
+def test_depth_order_is_stable_depth_sort():
+    scene, cam = c2_small()
+    img, fr, A = run_forward(scene, cam, "quadbox")
+    d = A["rgbd"][:, 3].astype(np.float32).view(np.uint32) & np.uint32(0x7FFFFFFF)
+    key = np.where(A["counts"] > 0, d, np.uint32(0x7FFFFFFF))
+    np.testing.assert_array_equal(A["depth_order"].view(np.uint32), np.argsort(key, kind="stable").astype(np.uint32))
+
+
+def test_sort_modes_identical_images():
+    scene, cam = c2_small()
+    a = run_forward(scene, cam, "quadbox", sort_mode="depth_first")
+    b = run_forward(scene, cam, "quadbox", sort_mode="full_key")
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[2]["vals"], b[2]["vals"])
+    np.testing.assert_array_equal(a[2]["ranges"], b[2]["ranges"])
 
 
 @pytest.mark.parametrize("maker", [c1_small, c2_small])
@@ -127,7 +146,7 @@ def test_ragged_image_and_tiny_scenes():
         assert ok, (W, H, n, st)
         if n:
             o = oracle_keys_from_gpu_boxes(A, O.QUADBOX, True, W, H)
-            np.testing.assert_array_equal(A["keys"].view(np.uint64), o["keys"])
+            np.testing.assert_array_equal(A["full_keys"], o["keys"])
 
 
 def test_huge_gaussian_covering_everything():
@@ -137,7 +156,7 @@ def test_huge_gaussian_covering_everything():
     scene["opacities"][0] = 3.0
     img, fr, A = run_forward(scene, cam, "quadbox")
     o = oracle_keys_from_gpu_boxes(A, O.QUADBOX, True, 300, 200)
-    np.testing.assert_array_equal(A["keys"].view(np.uint64), o["keys"])
+    np.testing.assert_array_equal(A["full_keys"], o["keys"])
     ok, st = image_parity(img, O.image(f64(scene), cam, O.QUADBOX))
     assert ok, st
 
@@ -184,7 +203,8 @@ def test_unsynchronised_pipeline_matches_synchronised():
     fr.check()
     np.testing.assert_array_equal(img_b.cpu().numpy(), img_a)
     B = fr.arrays(n_pairs=fr_a.n_pairs)
-    np.testing.assert_array_equal(B["keys"].cpu().numpy(), A["keys"])
+    np.testing.assert_array_equal(B["vals"].cpu().numpy(), A["vals"])
+    np.testing.assert_array_equal(B["tile_keys"].cpu().numpy(), A["tile_keys"])
 
 
 def test_invalid_arguments_rejected():
