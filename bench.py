@@ -296,11 +296,11 @@ def run_ours(args, rank, world, local_rank):
     result["roofline"] = roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode)
     tile_bits = (((W + 15) // 16) * ((H + 15) // 16) - 1).bit_length()
     if args.sort_mode == "depth_first":
-        per_fwd = 1 + (1 + 2 + 4) + 3 + 1 + (2 + -(-tile_bits // digit_bits)) + 1 + 1
+        per_fwd = 1 + (1 + 2 + 4) + 3 + 1 + 1 + -(-tile_bits // digit_bits) + 1
         per_other = 1 + 3 + 1 + (2 + -(-(31 + tile_bits) // 8)) + 1 + 1
     else:
         per_fwd = 1 + 3 + 1 + (2 + -(-(31 + tile_bits) // digit_bits)) + 1 + 1
-        per_other = 1 + (1 + 2 + 4) + 3 + 1 + (2 + -(-tile_bits // 8)) + 1 + 1
+        per_other = 1 + (1 + 2 + 4) + 3 + 1 + 1 + -(-tile_bits // 8) + 1
     # fwd and fwd+bwd phases for both binnings, the comparison phase, the e2e loop
     result["gpu_launches"] = args.steps * (2 * per_fwd + 2 * (per_fwd + 2) + per_other + per_fwd)
     if tune:
@@ -313,10 +313,10 @@ def stage_bytes(P, n, W, H, digit_bits, sort_mode):
     tiles = ((W + 15) // 16) * ((H + 15) // 16)
     tile_bits = (tiles - 1).bit_length()
     if sort_mode == "depth_first":
-        # tile sort: upfront histogram reads 4 B keys; each pass reads and
-        # writes 4 B key + 4 B value; ranges read 4 B keys
+        # tile sort: each pass reads and writes a 4 B key and a 4 B value (the
+        # bucket offsets and ranges come from the per-tile counts)
         passes = -(-tile_bits // digit_bits)
-        sort_bytes = P * (4 + passes * 16 + 4) + tiles * 8
+        sort_bytes = P * passes * 16
         # emit: depth keys (read 20 B, write 8 B per Gaussian), depth sort of n
         # 4-byte keys + values (4 passes), scan (read 8 B, write 4 B), box record
         # read (48 B), pairs written (8 B each)
@@ -351,7 +351,8 @@ def roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
                "evaluations": n_eval}
     else:
         ach = sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9
-        out = {"kernel": "onesweep_kernel (+hist, ranges)", "bound": "hbm", "achieved": round(ach, 1),
+        out = {"kernel": "onesweep_kernel (tile sort passes)" if sort_mode == "depth_first"
+               else "onesweep_kernel (+hist, ranges)", "bound": "hbm", "achieved": round(ach, 1),
                "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     # secondary: the HBM-bound stages

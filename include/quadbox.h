@@ -139,9 +139,9 @@ typedef struct {
     int32_t sort_digit_bits;  /* 8..11, radix digit width of qb_sort        */
     int32_t render_batch;     /* Gaussians staged per shared-memory batch   */
     int32_t sorted_in_alt;    /* internal: sorted pairs live in buffer 1    */
-    int32_t sort_mode;        /* qb_sort_mode; set before qb_bin_emit       */
+    int32_t sort_mode;        /* qb_sort_mode; set before qb_preprocess     */
     int32_t depth_in_alt;     /* internal: depth order lives in buffer 1    */
-    int32_t reserved[3];
+    int32_t reserved[3];      /* internal */
 } qb_frame;
 
 /* Device arrays inside a frame workspace (for inspection and tests).  All

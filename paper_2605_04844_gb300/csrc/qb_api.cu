@@ -77,6 +77,8 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     }
     L.dsort_scratch = take(db);
     L.ranges = take(8 * (size_t)tiles);
+    L.tile_diff = take(4 * (size_t)(tx + 1) * (ty + 1));
+    L.tile_single = take(4 * (size_t)tiles);
     L.tfinal = take(4 * (size_t)W * H);
     L.ncontrib = take(4 * (size_t)W * H);
     L.neval = take(4 * (size_t)W * H);
@@ -242,6 +244,8 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     a.opac = scene->opacities;
     a.sh = scene->sh;
     a.raw = scene->params_raw != 0;
+    a.sh_vec4 = reinterpret_cast<uintptr_t>(scene->sh) % 16 == 0;
+    a.quat_vec4 = reinterpret_cast<uintptr_t>(scene->quats) % 16 == 0;
     a.cam = to_cam(*camera);
     a.mode = base_mode;
     a.clamp3s = (mode & QB_BIN_NO_CLAMP) == 0;
@@ -252,7 +256,18 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     a.r3 = at<float>(frame, L.r3);
     a.meta = at<int>(frame, L.meta);
     a.counts = at<uint32_t>(frame, L.counts);
+    a.tiles_x = frame->tiles_x;
+    a.tile_diff = nullptr;
+    a.tile_single = nullptr;
+    if (frame->sort_mode == QB_SORT_DEPTH_FIRST) {
+        a.tile_diff = at<int>(frame, L.tile_diff);
+        a.tile_single = at<int>(frame, L.tile_single);
+        // the two count arrays are adjacent in the workspace: clear them together
+        QB_CUDA(cudaMemsetAsync(a.tile_diff, 0, L.tile_single - L.tile_diff + 4 * (size_t)frame->tiles_x * frame->tiles_y,
+                                (cudaStream_t)stream));
+    }
     QB_CUDA(launch_preprocess(a, scene->sh_degree, (cudaStream_t)stream));
+    frame->reserved[0] = frame->sort_mode;  // mode the tile counts were made for
     frame->bin_mode = mode;
     frame->sh_degree = scene->sh_degree;
     frame->stage = 1;
@@ -267,6 +282,10 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     if (frame->stage < 1) return fail(QB_ERR_STATE, "qb_bin_emit before qb_preprocess");
     if (frame->sort_mode != QB_SORT_DEPTH_FIRST && frame->sort_mode != QB_SORT_FULL_KEY)
         return fail(QB_ERR_INVALID_ARG, "sort_mode must be QB_SORT_DEPTH_FIRST or QB_SORT_FULL_KEY");
+    if (frame->sort_mode != frame->reserved[0])
+        return fail(QB_ERR_STATE, "sort_mode changed between qb_preprocess and qb_bin_emit");
+    if (frame->sort_digit_bits < 8 || frame->sort_digit_bits > kMaxDigitBits)
+        return fail(QB_ERR_INVALID_ARG, "sort_digit_bits must be 8..11");
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t *d_np = at<uint64_t>(frame, L.state);
     uint32_t *err = at<uint32_t>(frame, L.state + 8);
@@ -286,6 +305,16 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     }
     QB_CUDA(launch_scan(at<uint32_t>(frame, L.counts), perm, frame->n, at<uint32_t>(frame, L.offsets),
                         at<uint64_t>(frame, L.scan_part), d_np, s));
+    if (depth_first) {
+        // per-tile counts -> ranges and the tile sort's bucket offsets
+        const int tile_bits = frame->key_bits - kDepthBits;
+        const int passes = tile_bits > 0 ? (tile_bits + frame->sort_digit_bits - 1) / frame->sort_digit_bits : 0;
+        QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), frame->tiles_x,
+                                 frame->tiles_y,
+                                 at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
+                                 sort_hist_stride(), frame->sort_digit_bits, passes, s));
+        frame->reserved[1] = frame->sort_digit_bits;  // digit width the offsets were made for
+    }
     frame->n_pairs = UINT64_MAX;
     if (n_pairs_out) {
         uint64_t P = 0;
@@ -311,6 +340,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     a.offsets = at<uint32_t>(frame, L.offsets);
     a.vals = at<uint32_t>(frame, L.vals0);
     a.n_pairs = d_np;
+    a.n_pairs_host = frame->n_pairs;
     a.capacity = frame->pair_capacity;
     a.mode = frame->bin_mode & 0xff;
     a.clamp3s = (frame->bin_mode & QB_BIN_NO_CLAMP) == 0;
@@ -342,14 +372,16 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
     uint32_t *err = at<uint32_t>(frame, L.state + 8);
     if (frame->sort_mode == QB_SORT_DEPTH_FIRST) {
         // pairs were emitted in depth order: a stable sort on the tile id alone
+        // (bucket offsets and ranges came from the per-tile counts in qb_bin_emit)
+        if (frame->sort_digit_bits != frame->reserved[1])
+            return fail(QB_ERR_STATE, "sort_digit_bits changed between qb_bin_emit and qb_sort");
         const int tile_bits = frame->key_bits - kDepthBits;
         if (tile_bits > 0)
             QB_CUDA(sort_pairs(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
                                at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1), n_max, n_dev, tile_bits,
-                               frame->sort_digit_bits, at<void>(frame, L.sort_scratch), err, s, &passes));
+                               frame->sort_digit_bits, at<void>(frame, L.sort_scratch), err, s, &passes, true));
         frame->sorted_in_alt = passes & 1;
-        const uint32_t *sorted = at<uint32_t>(frame, frame->sorted_in_alt ? L.keys1 : L.keys0);
-        QB_CUDA(launch_ranges<uint32_t>(sorted, n_max, n_dev, at<uint2>(frame, L.ranges), ntiles, s));
+        (void)ntiles;
     } else {
         QB_CUDA(sort_pairs(at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint64_t>(frame, L.keys1),
                            at<uint32_t>(frame, L.vals1), n_max, n_dev, frame->key_bits, frame->sort_digit_bits,

@@ -24,6 +24,19 @@ namespace qb {
 
 constexpr int kBwdThreads = kTile * kTile;
 
+// float -> double by rebuilding the IEEE-754 bit pattern with integer
+// operations (exponent rebias 127 -> 1023, mantissa 23 -> 52 bits), so the
+// float64 atomics below need no float64 arithmetic in the SM; float32
+// subnormals (|v| < 1.2e-38) become zero.
+__device__ __forceinline__ double widen(float v) {
+    const uint32_t u = __float_as_uint(v);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                          ((uint64_t)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -32,7 +45,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
     __shared__ uint32_t s_id[kBwdThreads];
-    __shared__ float2 s_xy[kBwdThreads];
+    __shared__ float4 s_xy[kBwdThreads];  // mu_x, mu_y, skip threshold
     __shared__ float4 s_co[kBwdThreads];
     __shared__ float4 s_rgb[kBwdThreads];
     __shared__ int s_maxlast;
@@ -70,8 +83,10 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
         if (tid < cnt) {
             const uint32_t g = a.vals[rstart + start + tid];
             s_id[tid] = g;
-            s_xy[tid] = a.xy[g];
-            s_co[tid] = a.conic_o[g];
+            const float2 m = a.xy[g];
+            const float4 co = a.conic_o[g];
+            s_xy[tid] = make_float4(m.x, m.y, skip_threshold(co.w), 0.f);
+            s_co[tid] = co;
             s_rgb[tid] = a.rgbd[g];
         }
         __syncthreads();
@@ -80,11 +95,11 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
             float gv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
             if (p < last) {
-                const float2 m = s_xy[j];
+                const float4 m = s_xy[j];
                 const float4 co = s_co[j];
                 const float dx = m.x - pxf, dy = m.y - pyf;
                 const float power = eval_power(co, dx, dy);
-                if (power <= 0.f) {
+                if (power <= 0.f && power >= m.z) {
                     const float G = __expf(power);
                     const float oG = __fmul_rn(co.w, G);
                     const float alpha = fminf(kAlphaMax, oG);
@@ -127,7 +142,7 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
                     double *dst = a.g_screen + (size_t)s_id[j] * 9;
 #pragma unroll
                     for (int v = 0; v < 9; ++v)
-                        if (gv[v] != 0.f) atomicAdd(dst + v, (double)gv[v]);
+                        if (gv[v] != 0.f) atomicAdd(dst + v, widen(gv[v]));
                 }
             }
         }

@@ -148,92 +148,140 @@ __device__ __forceinline__ uint32_t lanemask_le() {
 
 constexpr int kEmitWarps = 8;
 constexpr int kSegPerWarp = 32 * 7;
+constexpr uint32_t kEmitChunk = 2048;  // output positions per warp
 
-// K3 (QPass modes and the single-box modes): each warp takes 32 consecutive
-// Gaussians of the emission order, decomposes each one's QPass traversal into
-// its segments (runs of scan lines with one merged interval), and then writes
-// the warp's whole output range 32 consecutive pairs at a time: lane q of a
-// chunk finds the segment holding its position from a ballot of the segment
-// starts that fall in the chunk, and derives its tile from the position
-// within that segment.  Stores are contiguous across the warp.
+// K3 (QPass modes and the single-box modes), balanced over the output: warp w
+// owns the pair positions [w C, (w+1) C).  It finds the first Gaussian whose
+// run reaches into that range (32-ary search over the emission-order
+// offsets), then takes the following Gaussians 32 at a time: each lane
+// decomposes its Gaussian's QPass traversal into segments (runs of scan lines
+// with one merged interval), and the warp writes the range 32 consecutive
+// positions at a time; lane q finds the segment holding its position from a
+// ballot of the segment starts that fall in its group.  Stores are contiguous
+// across the warp, and every warp writes at most C pairs however large the
+// Gaussians are.
 template <typename KeyT>
 __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, KeyT *__restrict__ keys) {
-    __shared__ uint32_t s_start[kEmitWarps][kSegPerWarp];
+    __shared__ int32_t s_start[kEmitWarps][kSegPerWarp];
     __shared__ uint32_t s_geo[kEmitWarps][kSegPerWarp];
     __shared__ uint32_t s_len[kEmitWarps][kSegPerWarp];
+    __shared__ float s_inv[kEmitWarps][kSegPerWarp];
     __shared__ uint32_t s_gid[kEmitWarps][32];
     __shared__ uint32_t s_dbits[kEmitWarps][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t j = ((size_t)blockIdx.x * kEmitWarps + wid) * 32 + lane;
-    if (*a.n_pairs > a.capacity) {
-        if (j == 0) atomicOr(a.err, kErrCapacity);
+    const uint64_t P = *a.n_pairs;
+    const uint64_t warp_id = (uint64_t)blockIdx.x * kEmitWarps + wid;
+    if (P > a.capacity) {
+        if (warp_id == 0 && lane == 0) atomicOr(a.err, kErrCapacity);
         return;
     }
-    uint32_t gid = 0, cnt = 0, off = 0;
-    if (j < (size_t)a.n) {
-        gid = a.perm ? a.perm[j] : (uint32_t)j;
-        cnt = a.counts[gid];
-        off = a.offsets[j];
-    }
-    const uint32_t base = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t total = __reduce_add_sync(0xffffffffu, cnt);
-    if (total == 0u) return;
+    const uint64_t C = warp_id * kEmitChunk;
+    if (C >= P || a.n == 0) return;
+    const int32_t L = (int32_t)min((uint64_t)kEmitChunk, P - C);
 
-    QSeg seg[7];
-    int ns = 0;
-    bool columns = false;
-    uint32_t dbits = 0;
-    if (cnt > 0u) {
-        const float2 xy = a.xy[gid];
-        const int meta = a.meta[gid];
-        dbits = __float_as_uint(a.rgbd[gid].w) & 0x7fffffffu;
-        Rect r[4];
-        box_rects(xy.x, xy.y, a.box[gid], a.r3[gid], (meta & kMetaOrient) != 0, a.mode, a.clamp3s, a.W, a.H, r);
-        QPass qp;
-        if (qpass_setup(r, qp)) {
-            ns = qpass_segments(qp, seg);
-            columns = qp.columns;
-        }
+    // last emission position j with offsets[j] <= C (offsets are non-decreasing)
+    int64_t lo = 0, hi = a.n - 1;  // invariant: offsets[lo] <= C, answer in [lo, hi]
+    while (hi > lo) {
+        const int64_t span = hi - lo;
+        const int64_t probe = lo + (span * (lane + 1) + 31) / 32;  // 32 probes in (lo, hi]
+        const bool le = probe <= hi && (uint64_t)a.offsets[probe] <= C;
+        const uint32_t m = __ballot_sync(0xffffffffu, le);
+        const int k = m ? 31 - __clz(m) : -1;  // highest probing lane with offsets <= C
+        const int64_t new_lo = k >= 0 ? lo + (span * (k + 1) + 31) / 32 : lo;
+        const int64_t nk = k + 1;
+        const int64_t new_hi = nk < 32 ? lo + (span * (nk + 1) + 31) / 32 - 1 : hi;
+        lo = new_lo;
+        const int64_t cand_hi = new_hi > new_lo ? new_hi : new_lo;
+        hi = cand_hi < hi ? cand_hi : hi;
     }
-    s_gid[wid][lane] = gid;
-    s_dbits[wid][lane] = dbits;
-    const int sincl = warp_incl_scan(ns);
-    const int sbase = sincl - ns;
-    const int nseg = __shfl_sync(0xffffffffu, sincl, 31);
-    uint32_t rel = off - base;
-    for (int q = 0; q < ns; ++q) {
-        s_start[wid][sbase + q] = rel;
-        s_geo[wid][sbase + q] = (uint32_t)seg[q].s0 | ((uint32_t)seg[q].lo << 16);
-        s_len[wid][sbase + q] = (uint32_t)seg[q].len | ((uint32_t)lane << 16) | ((uint32_t)columns << 24);
-        rel += (uint32_t)(seg[q].nl * seg[q].len);
-    }
-    __syncwarp();
+    int64_t j0 = lo;
 
-    const uint32_t le = lanemask_le();
+    const uint32_t le_mask = lanemask_le();
     const uint32_t tx_n = (uint32_t)a.tiles_x;
-    int cur = -1;  // last segment starting before the current chunk
-    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
-        const int cand = cur + 1 + lane;
-        uint32_t bit = 0u;
-        if (cand < nseg) {
-            const uint32_t st = s_start[wid][cand];
-            if (st < c0 + 32u) bit = 1u << (st - c0);
+    int32_t done_to = 0;  // chunk positions [0, done_to) written
+    while (done_to < L && j0 < a.n) {
+        const int64_t j = j0 + lane;
+        uint32_t gid = 0, cnt = 0;
+        int64_t rel = (int64_t)1 << 40;
+        if (j < a.n) {
+            gid = a.perm ? a.perm[j] : (uint32_t)j;
+            cnt = a.counts[gid];
+            rel = (int64_t)a.offsets[j] - (int64_t)C;
         }
-        const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
-        const uint32_t p = c0 + lane;
-        if (p < total) {
-            const int idx = cur + __popc(M & le);
-            const uint32_t st = s_start[wid][idx], geo = s_geo[wid][idx], ln = s_len[wid][idx];
-            const uint32_t k = p - st, len = ln & 0xffffu;
-            const uint32_t line = (geo & 0xffffu) + k / len;
-            const uint32_t u = (geo >> 16) + k % len;
-            const bool cols = (ln >> 24) & 1u;
-            const uint32_t owner = (ln >> 16) & 0xffu;
-            const uint32_t tile = (cols ? u : line) * tx_n + (cols ? line : u);
-            keys[base + p] = make_key<KeyT>(tile, s_dbits[wid][owner]);
-            a.vals[base + p] = s_gid[wid][owner];
+        const bool relevant = cnt > 0u && rel < L && rel + (int64_t)cnt > 0;
+        QSeg seg[7];
+        int ns = 0;
+        bool columns = false;
+        uint32_t dbits = 0;
+        if (relevant) {
+            const float2 xy = a.xy[gid];
+            const int meta = a.meta[gid];
+            dbits = __float_as_uint(a.rgbd[gid].w) & 0x7fffffffu;
+            Rect r[4];
+            box_rects(xy.x, xy.y, a.box[gid], a.r3[gid], (meta & kMetaOrient) != 0, a.mode, a.clamp3s, a.W, a.H,
+                      r);
+            QPass qp;
+            if (qpass_setup(r, qp)) {
+                ns = qpass_segments(qp, seg);
+                columns = qp.columns;
+            }
         }
-        cur += __popc(M);
+        __syncwarp();
+        s_gid[wid][lane] = gid;
+        s_dbits[wid][lane] = dbits;
+        const int sincl = warp_incl_scan(ns);
+        const int sbase = sincl - ns;
+        const int nseg = __shfl_sync(0xffffffffu, sincl, 31);
+        int32_t r0 = (int32_t)(rel > -((int64_t)1 << 30) ? rel : -((int64_t)1 << 30));
+        for (int q = 0; q < ns; ++q) {
+            s_start[wid][sbase + q] = r0;
+            s_geo[wid][sbase + q] = (uint32_t)seg[q].s0 | ((uint32_t)seg[q].lo << 16);
+            s_len[wid][sbase + q] = (uint32_t)seg[q].len | ((uint32_t)lane << 16) | ((uint32_t)columns << 24);
+            s_inv[wid][sbase + q] = 1.0f / (float)seg[q].len;
+            r0 += seg[q].nl * seg[q].len;
+        }
+        // end of this batch's pairs within the chunk
+        const int64_t last_end = __shfl_sync(0xffffffffu, rel + (int64_t)cnt, 31);
+        const int32_t batch_end = (int32_t)(last_end < (int64_t)L ? last_end : (int64_t)L);
+        __syncwarp();
+        // cur: last segment starting at or before done_to
+        int cur = -1;
+        for (int b = 0; b < nseg; b += 32) {
+            const bool le = b + lane < nseg && s_start[wid][b + lane] <= done_to;
+            cur += __popc(__ballot_sync(0xffffffffu, le));
+        }
+        for (int32_t c0 = done_to; c0 < batch_end; c0 += 32) {
+            const int cand = cur + 1 + lane;
+            uint32_t bit = 0u;
+            if (cand < nseg) {
+                const int32_t st = s_start[wid][cand];
+                if (st < c0 + 32) bit = 1u << (st - c0);
+            }
+            const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
+            const int32_t p = c0 + lane;
+            if (p < batch_end) {
+                const int idx = cur + __popc(M & le_mask);
+                const int32_t st = s_start[wid][idx];
+                const uint32_t geo = s_geo[wid][idx], ln = s_len[wid][idx];
+                const uint32_t k = (uint32_t)(p - st), len = ln & 0xffffu;
+                // k / len through the reciprocal (k < 2^24, so the estimate is
+                // off by at most one) and one exact correction
+                int32_t q = (int32_t)((float)k * s_inv[wid][idx]);
+                int32_t r = (int32_t)k - q * (int32_t)len;
+                if (r < 0) { --q; r += (int32_t)len; }
+                if (r >= (int32_t)len) { ++q; r -= (int32_t)len; }
+                const uint32_t line = (geo & 0xffffu) + (uint32_t)q;
+                const uint32_t u = (geo >> 16) + (uint32_t)r;
+                const bool cols = (ln >> 24) & 1u;
+                const uint32_t owner = (ln >> 16) & 0xffu;
+                const uint32_t tile = (cols ? u : line) * tx_n + (cols ? line : u);
+                keys[C + p] = make_key<KeyT>(tile, s_dbits[wid][owner]);
+                a.vals[C + p] = s_gid[wid][owner];
+            }
+            cur += __popc(M);
+        }
+        done_to = max(done_to, batch_end);
+        j0 += 32;
     }
 }
 
@@ -279,8 +327,11 @@ cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s) {
     if (a.mode == QB_BIN_QUADBOX_NAIVE) {
         emit_naive_kernel<KeyT><<<(a.n + 255) / 256, 256, 0, s>>>(a, keys);
     } else {
-        const int per_block = kEmitWarps * 32;
-        emit_warp_kernel<KeyT><<<(a.n + per_block - 1) / per_block, per_block, 0, s>>>(a, keys);
+        const uint64_t pairs = a.n_pairs_host != UINT64_MAX ? a.n_pairs_host : a.capacity;
+        const uint64_t warps = (pairs + kEmitChunk - 1) / kEmitChunk;
+        const uint64_t blocks = (warps + kEmitWarps - 1) / kEmitWarps;
+        if (blocks > 0) emit_warp_kernel<KeyT><<<(unsigned)blocks, kEmitWarps * 32, 0, s>>>(a, keys);
+        else if (a.n > 0) emit_warp_kernel<KeyT><<<1, kEmitWarps * 32, 0, s>>>(a, keys);  // flags overflow
     }
     return cudaGetLastError();
 }
@@ -315,6 +366,70 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
     uint64_t blocks = (n_max + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     ranges_kernel<KeyT><<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges, (uint32_t)ntiles);
+    return cudaGetLastError();
+}
+
+// Per-tile pair counts from the difference array written by the preprocess:
+// a 2D prefix sum plus the single-tile counts gives each tile's count; an exclusive scan over tile ids
+// gives the ranges of the tile-sorted pairs; the counts summed per digit give
+// the exclusive bucket offsets of every pass of the tile sort.  One block.
+__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, int tx, int ty, uint2 *ranges,
+                                                         uint32_t *hist, int hist_stride, int rb, int passes) {
+    extern __shared__ uint32_t sh_hist[];  // passes * 2^rb
+    const int R = 1 << rb;
+    const int stride = tx + 1;
+    for (int j = threadIdx.x; j < passes * R; j += blockDim.x) sh_hist[j] = 0u;
+    for (int y = threadIdx.x; y < ty; y += blockDim.x) {
+        int run = 0;
+        for (int x = 0; x < tx; ++x) {
+            run += D[y * stride + x];
+            D[y * stride + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < tx; x += blockDim.x) {
+        int run = 0;
+        for (int y = 0; y < ty; ++y) {
+            run += D[y * stride + x];
+            D[y * stride + x] = run + single[y * tx + x];
+        }
+    }
+    __syncthreads();
+    // exclusive scan of the counts over tile ids, each thread a contiguous chunk
+    const int ntiles = tx * ty;
+    const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
+    uint32_t local = 0;
+    for (int t = t0; t < t1; ++t) local += (uint32_t)D[(t / tx) * stride + t % tx];
+    uint32_t total;
+    uint32_t run = block_incl_scan<uint32_t>(local, &total) - local;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = (uint32_t)D[(t / tx) * stride + t % tx];
+        ranges[t] = c ? make_uint2(run, run + c) : make_uint2(0u, 0u);  // [0,0) for an empty tile
+        run += c;
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh_hist[p * R + ((t >> (p * rb)) & (R - 1))], c);
+    }
+    __syncthreads();
+    // exclusive offsets per pass
+    for (int p = 0; p < passes; ++p) {
+        const int per_d = (R + blockDim.x - 1) / blockDim.x;
+        const int d0 = threadIdx.x * per_d, d1 = min(R, d0 + per_d);
+        uint32_t s = 0;
+        for (int d = d0; d < d1; ++d) s += sh_hist[p * R + d];
+        uint32_t tot;
+        uint32_t r = block_incl_scan<uint32_t>(s, &tot) - s;
+        for (int d = d0; d < d1; ++d) {
+            hist[p * hist_stride + d] = r;
+            r += sh_hist[p * R + d];
+        }
+    }
+}
+
+cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, int tiles_x, int tiles_y, uint2 *ranges,
+                             uint32_t *hist, int hist_stride, int digit_bits, int passes, cudaStream_t s) {
+    const size_t smem = (size_t)passes * ((size_t)1 << digit_bits) * 4;
+    tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, tiles_x, tiles_y, ranges, hist, hist_stride,
+                                           digit_bits, passes);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,8 @@ struct Layout {
     size_t sort_scratch, sort_scratch_bytes;
     size_t dkeys0, dkeys1, dvals0, dvals1, dsort_scratch;  // depth order of the Gaussians
     size_t ranges, tfinal, ncontrib, neval;
+    size_t tile_diff;  // (tiles_y+1) x (tiles_x+1) int difference array
+    size_t tile_single;  // tiles ints: pair counts of single-tile Gaussians
     size_t gscreen;  // [n][9] screen-space gradients
     size_t state;  // u64 n_pairs, u32 err_flags, padding
     size_t total;
@@ -61,12 +63,22 @@ size_t sort_scratch_bytes(uint64_t n, int end_bit, int digit_bits);
 cudaError_t sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                        uint64_t n_max, const uint64_t *n_dev, int end_bit, int digit_bits,
                        void *scratch, uint32_t *err_flags, cudaStream_t stream, int *passes_out);
-// The same sort on 32-bit keys (end_bit <= 32).
+// The same sort on 32-bit keys (end_bit <= 32).  With hist_ready the
+// exclusive bucket offsets of every pass are already in the scratch's
+// histogram table (sort_hist_table, stride sort_hist_stride per pass).
 cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                        uint64_t n_max, const uint64_t *n_dev, int end_bit, int digit_bits,
-                       void *scratch, uint32_t *err_flags, cudaStream_t stream, int *passes_out);
+                       void *scratch, uint32_t *err_flags, cudaStream_t stream, int *passes_out,
+                       bool hist_ready = false);
+uint32_t *sort_hist_table(void *scratch);
+int sort_hist_stride();
 
 // ---- device helpers -----------------------------------------------------------
+// Exponents below this give alpha = o e^power < (1/255) e^-0.001: the 1e-3
+// margin is far wider than the float32 error of the alpha test, so skipping
+// them first never changes a decision of that test.
+__device__ __forceinline__ float skip_threshold(float o) { return -logf(255.0f * o) - 1e-3f; }
+
 // Exponent of the 2D Gaussian at offset (dx, dy) = mu^2D - pixel:
 // -(a dx^2 + c dy^2)/2 - b dx dy.  The operation sequence is spelled out with
 // intrinsics so the forward and backward kernels take identical decisions.

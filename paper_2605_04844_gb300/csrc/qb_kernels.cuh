@@ -9,6 +9,8 @@ struct PreArgs {
     int n;
     const float *means, *scales, *quats, *opac, *sh;
     bool raw;
+    bool sh_vec4;    // sh rows may be read as float4 (16-byte aligned)
+    bool quat_vec4;  // quats may be read as float4 (16-byte aligned)
     CamDev cam;
     int mode;
     bool clamp3s;
@@ -17,6 +19,9 @@ struct PreArgs {
     float *r3;
     int *meta;
     uint32_t *counts;
+    int *tile_diff;    // [(tiles_y+1)][(tiles_x+1)] difference array of per-tile pair counts, or null
+    int *tile_single;  // [tiles] pair counts of single-tile Gaussians
+    int tiles_x;
 };
 
 struct EmitArgs {
@@ -31,6 +36,7 @@ struct EmitArgs {
     const uint32_t *offsets;  // by emission position
     uint32_t *vals;
     const uint64_t *n_pairs;
+    uint64_t n_pairs_host;  // P when the host knows it, else UINT64_MAX
     uint64_t capacity;
     int mode;
     bool clamp3s;
@@ -85,6 +91,8 @@ cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s);
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges, int ntiles,
                           cudaStream_t s);
+cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, int tiles_x, int tiles_y, uint2 *ranges,
+                             uint32_t *hist, int hist_stride, int digit_bits, int passes, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs &a, int batch, cudaStream_t s);
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s);

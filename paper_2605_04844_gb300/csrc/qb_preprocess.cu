@@ -17,9 +17,14 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     const CamDev &cam = a.cam;
     const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
     Proj p;
-    bool ok = project_gaussian(cam, m0, m1, m2, a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2],
-                               a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3],
-                               a.raw, p);
+    float4 q4;
+    if (a.quat_vec4) {
+        q4 = __ldg(reinterpret_cast<const float4 *>(a.quats) + i);
+    } else {
+        q4 = make_float4(a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]);
+    }
+    bool ok = project_gaussian(cam, m0, m1, m2, a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2], q4.x,
+                               q4.y, q4.z, q4.w, a.raw, p);
     if (ok) {
         float ov = a.opac[i];
         p.o = a.raw ? 1.0f / (1.0f + expf(-ov)) : ov;
@@ -40,11 +45,31 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     sh_eval<DEG>(dx * inv, dy * inv, dz * inv, Y);
     const float *sh = a.sh + (size_t)i * (K * 3);
     float rgb[3] = {0.5f, 0.5f, 0.5f};
+    if ((K * 3) % 4 == 0 && a.sh_vec4) {
+        // 16-byte loads of the coefficient row (3K floats, K even)
+        float c[K * 3];
+        const float4 *sh4 = reinterpret_cast<const float4 *>(sh);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        rgb[0] = fmaf(Y[k], __ldg(sh + 3 * k), rgb[0]);
-        rgb[1] = fmaf(Y[k], __ldg(sh + 3 * k + 1), rgb[1]);
-        rgb[2] = fmaf(Y[k], __ldg(sh + 3 * k + 2), rgb[2]);
+        for (int q = 0; q < (K * 3) / 4; ++q) {
+            const float4 v = __ldg(sh4 + q);
+            c[4 * q] = v.x;
+            c[4 * q + 1] = v.y;
+            c[4 * q + 2] = v.z;
+            c[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            rgb[0] = fmaf(Y[k], c[3 * k], rgb[0]);
+            rgb[1] = fmaf(Y[k], c[3 * k + 1], rgb[1]);
+            rgb[2] = fmaf(Y[k], c[3 * k + 2], rgb[2]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            rgb[0] = fmaf(Y[k], __ldg(sh + 3 * k), rgb[0]);
+            rgb[1] = fmaf(Y[k], __ldg(sh + 3 * k + 1), rgb[1]);
+            rgb[2] = fmaf(Y[k], __ldg(sh + 3 * k + 2), rgb[2]);
+        }
     }
     int meta = kMetaVisible | (bt.orient ? kMetaOrient : 0);
 #pragma unroll
@@ -58,17 +83,33 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     Rect rects[4];
     box_rects(p.mx, p.my, bt.box, bt.r3, bt.orient, a.mode, a.clamp3s, cam.W, cam.H, rects);
     uint32_t cnt = 0;
-    if (a.mode == QB_BIN_QUADBOX_NAIVE) {
-        cnt = naive_count(rects);
-    } else {
+    QPass qp;
+    if (qpass_setup(rects, qp)) {
+        QSeg seg[7];
+        const int ns = qpass_segments(qp, seg);
         // QPass count: the lines of each run of equal intervals times its length
-        QPass qp;
-        if (qpass_setup(rects, qp)) {
-            QSeg seg[7];
-            const int ns = qpass_segments(qp, seg);
-            for (int q = 0; q < ns; ++q) cnt += (uint32_t)(seg[q].nl * seg[q].len);
+        for (int q = 0; q < ns; ++q) cnt += (uint32_t)(seg[q].nl * seg[q].len);
+        if (a.tile_diff && cnt == 1u) {
+            // one tile (the common case): count it directly
+            const int t = qp.columns ? seg[0].lo * a.tiles_x + seg[0].s0 : seg[0].s0 * a.tiles_x + seg[0].lo;
+            atomicAdd(a.tile_single + t, 1);
+        } else if (a.tile_diff) {
+            // per-tile pair counts as a 2D difference array: +1/-1 at the corners
+            // of every rectangle of the Gaussian's tile set
+            const int stride = a.tiles_x + 1;
+            for (int q = 0; q < ns; ++q) {
+                const int l0 = seg[q].s0, l1 = seg[q].s0 + seg[q].nl - 1;
+                const int u0 = seg[q].lo, u1 = seg[q].lo + seg[q].len - 1;
+                const int x0 = qp.columns ? l0 : u0, x1 = qp.columns ? l1 : u1;
+                const int y0 = qp.columns ? u0 : l0, y1 = qp.columns ? u1 : l1;
+                atomicAdd(a.tile_diff + y0 * stride + x0, 1);
+                atomicAdd(a.tile_diff + y0 * stride + x1 + 1, -1);
+                atomicAdd(a.tile_diff + (y1 + 1) * stride + x0, -1);
+                atomicAdd(a.tile_diff + (y1 + 1) * stride + x1 + 1, 1);
+            }
         }
     }
+    if (a.mode == QB_BIN_QUADBOX_NAIVE) cnt = naive_count(rects);  // the same set, counted the naive way
 
     a.xy[i] = make_float2(p.mx, p.my);
     a.conic_o[i] = make_float4(p.a, p.b, p.c, p.o);

@@ -5,7 +5,8 @@
 // depth-sorted Gaussian list is walked in batches: each thread stages one
 // Gaussian (mu^2D, conic+opacity, colour) into shared memory, then every
 // pixel consumes the batch.  Per entry (3DGS conventions):
-//   q = a dx^2 + 2 b dx dy + c dy^2, skip if -q/2 > 0;
+//   q = a dx^2 + 2 b dx dy + c dy^2, skip if -q/2 > 0 (and, before the exp,
+//   skip exponents so low that alpha is certainly below 1/255);
 //   alpha = min(0.99, o exp(-q/2)), skip if alpha < 1/255;
 //   T' = T (1 - alpha); stop before adding once T' < 1e-4;
 //   C += alpha T c; T = T'.
@@ -17,7 +18,7 @@ namespace qb {
 constexpr int kRenderThreads = kTile * kTile;
 
 __global__ void __launch_bounds__(kRenderThreads) render_kernel(RenderArgs a) {
-    __shared__ float2 s_xy[kRenderThreads];
+    __shared__ float4 s_xy[kRenderThreads];  // mu_x, mu_y, skip threshold on the exponent
     __shared__ float4 s_co[kRenderThreads];
     __shared__ float4 s_rgb[kRenderThreads];
 
@@ -40,19 +41,21 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(RenderArgs a) {
         const int idx = base + tid;
         if (idx < total) {
             const uint32_t g = a.vals[range.x + idx];
-            s_xy[tid] = a.xy[g];
-            s_co[tid] = a.conic_o[g];
+            const float2 m = a.xy[g];
+            const float4 co = a.conic_o[g];
+            s_xy[tid] = make_float4(m.x, m.y, skip_threshold(co.w), 0.f);
+            s_co[tid] = co;
             s_rgb[tid] = a.rgbd[g];
         }
         __syncthreads();
         const int cnt = min(kRenderThreads, total - base);
         for (int j = 0; !done && j < cnt; ++j) {
             ++contributor;
-            const float2 m = s_xy[j];
+            const float4 m = s_xy[j];
             const float4 co = s_co[j];
             const float dx = m.x - pxf, dy = m.y - pyf;
             const float power = eval_power(co, dx, dy);
-            if (power > 0.f) continue;
+            if (power > 0.f || power < m.z) continue;  // m.z: alpha certainly below 1/255
             const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, __expf(power)));
             if (alpha < kAlphaMin) continue;
             const float testT = __fmul_rn(T, 1.f - alpha);

@@ -7,8 +7,8 @@
 // Each digit pass then reads and writes the pairs once: a block takes the
 // next tile of 4096 keys (tile order = launch order through an atomic
 // counter, so every earlier tile belongs to a block that is already
-// running), ranks its keys per warp with match-any, publishes its digit
-// counts, looks back over earlier tiles for their running totals, and
+// running), counts its digits, publishes the counts and looks back over
+// earlier tiles for their running totals, ranks its keys per warp, and
 // scatters keys then values through shared memory so that runs of equal
 // digits leave as contiguous stores.  Every look-back spin is bounded; on
 // expiry it raises kErrTimeout and still publishes, so no block waits forever.
@@ -18,14 +18,15 @@
 
 namespace qb {
 
-constexpr int kSortBlock = 256;
+constexpr int kSortBlock = 512;
 constexpr int kSortWarps = kSortBlock / 32;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortBlock * kSortItems;  // 4096 keys per block
+constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookWindow = 8;  // status words fetched per look-back step
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
-constexpr int kSpinLimit = 1 << 22;
 constexpr int kHistStride = 1 << kMaxDigitBits;  // per-pass stride of the histogram table
 constexpr size_t kSortHeader = (size_t)kMaxPasses * kHistStride * 4 + 256;
 
@@ -96,6 +97,8 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const KeyT *__restrict__
         const KeyT k = keys[idx];
         for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * R + (int)((k >> (p * RB)) & (R - 1))], 1u);
     }
+    // (keys from the depth-first emit are spatially coherent: many lanes of a
+    // warp share a digit; the shared-memory atomics serialise them in hardware)
     __syncthreads();
     for (int j = threadIdx.x; j < passes * R; j += blockDim.x) {
         uint32_t v = sh[j];
@@ -128,9 +131,14 @@ __global__ void __launch_bounds__(1024) sort_hist_scan_kernel(uint32_t *hist) {
 
 template <int RB, typename KeyT>
 constexpr size_t onesweep_smem() {
-    return (size_t)kSortTile * sizeof(KeyT) + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)2 * (1 << RB) * 4;
+    return (size_t)kSortTile * sizeof(KeyT) + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)3 * (1 << RB) * 4;
 }
 
+// One digit pass.  Order of work inside a block: load the tile, count its
+// digits (shared atomics, order-free), publish the counts and look back at
+// once -- so successors never wait for this block's ranking -- then rank the
+// keys within each warp in their original order, and scatter keys and values
+// through shared memory.
 template <int RB, typename KeyT>
 __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__restrict__ kin,
                                                               const uint32_t *__restrict__ vin,
@@ -148,11 +156,13 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__rest
     uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem + (size_t)kSortTile * sizeof(KeyT));
     uint32_t *s_gbase = reinterpret_cast<uint32_t *>(s_whist + kSortWarps * R);
     uint32_t *s_lstart = s_gbase + R;
+    uint32_t *s_bcount = s_lstart + R;
     __shared__ uint32_t s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     for (int j = tid; j < kSortWarps * R / 2; j += kSortBlock) reinterpret_cast<uint32_t *>(s_whist)[j] = 0u;
+    for (int j = tid; j < R; j += kSortBlock) s_bcount[j] = 0u;
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t n = n_dev ? min(*n_dev, n_max) : n_max;
@@ -175,41 +185,24 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__rest
         val[k] = idx < n ? __ldcs(vin + idx) : 0u;
     }
 
-    // ---- rank within the warp, in original order ----
-    uint16_t *wh = s_whist + wid * R;
-    const uint32_t lt = lanemask_lt();
+    // ---- early digit counts of the tile ----
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const bool valid = wbase + 32 * k + lane < n;
-        const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & MASK : (uint32_t)R;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t pre = valid ? (uint32_t)wh[d] : 0u;
-        const uint32_t lower = __popc(peers & lt);
-        __syncwarp();
-        if (valid && lower == 0) wh[d] = (uint16_t)(pre + __popc(peers));
-        __syncwarp();
-        rank[k] = pre + lower;
-    }
+    for (int k = 0; k < kSortItems; ++k)
+        if (wbase + 32 * k + lane < n) atomicAdd(&s_bcount[(uint32_t)(key[k] >> shift) & MASK], 1u);
     __syncthreads();
 
-    // ---- per digit: warp exclusive prefix and block count ----
-    for (int d = tid; d < R; d += kSortBlock) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            uint32_t c = s_whist[w * R + d];
-            s_whist[w * R + d] = (uint16_t)run;
-            run += c;
-        }
-        s_gbase[d] = run;
-    }
-    __syncthreads();
-
+    // ---- publish, look back, publish the inclusive prefix ----
+    // One status word per (tile, digit): a 2-bit flag (aggregate = the tile's
+    // own count, inclusive = running total through the tile) and a 30-bit
+    // count.  Each thread walks back for its digits, kLookWindow words at a
+    // time (their addresses do not depend on what is read), adding aggregates
+    // until it meets an inclusive total; when the next word is not yet
+    // published it polls that word alone, sleeping between polls.
     uint32_t cnt[PER], tsum = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         int d = tid * PER + j;
-        cnt[j] = d < R ? s_gbase[d] : 0u;
+        cnt[j] = d < R ? s_bcount[d] : 0u;
         tsum += cnt[j];
     }
     uint32_t *lb = lookback + (size_t)tile * R;
@@ -220,42 +213,86 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__rest
     }
     uint32_t btotal;
     uint32_t run = block_excl_scan_u32(tsum, &btotal);  // contains __syncthreads
-    uint32_t ex[PER];
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         int d = tid * PER + j;
-        ex[j] = 0u;
         if (d >= R) continue;
         s_lstart[d] = run;
         run += cnt[j];
+        uint32_t acc = 0;
         if (tile > 0) {
-            uint32_t acc = 0;
             int64_t t = (int64_t)tile - 1;
             int spins = 0;
-            while (t >= 0) {
-                uint32_t sv = ld_relaxed(lookback + (size_t)t * R + d);
-                uint32_t f = sv & ~kCountMask;
-                if (f == 0u) {
-                    if (++spins > kSpinLimit) {
+            bool done = false;
+            while (!done && t >= 0) {
+                uint32_t sv[kLookWindow];
+#pragma unroll
+                for (int w = 0; w < kLookWindow; ++w)
+                    sv[w] = (t - w >= 0) ? ld_relaxed(lookback + (size_t)(t - w) * R + d) : kFlagIncl;
+                int used = 0;
+#pragma unroll
+                for (int w = 0; w < kLookWindow; ++w) {
+                    if (done || used < w) continue;  // stopped at an unpublished word
+                    const uint32_t f = sv[w] & ~kCountMask;
+                    if (f == 0u) continue;
+                    acc += sv[w] & kCountMask;
+                    used = w + 1;
+                    if (f == kFlagIncl) done = true;
+                }
+                t -= used;
+                if (!done && used == 0) {
+                    // the nearest earlier tile has not published this digit yet
+                    unsigned ns = 32;
+                    while ((ld_relaxed(lookback + (size_t)t * R + d) & ~kCountMask) == 0u) {
+                        if (++spins > kSpinLimit) break;
+                        __nanosleep(ns);
+                        ns = ns < 512 ? 2 * ns : 512;
+                    }
+                    if (spins > kSpinLimit) {
                         atomicOr(err, kErrTimeout);
                         break;
                     }
-                    if (spins > 64) __nanosleep(64);
-                    continue;
                 }
-                acc += sv & kCountMask;
-                if (f == kFlagIncl) break;
-                --t;
             }
             st_relaxed(lb + d, kFlagIncl | ((acc + cnt[j]) & kCountMask));
-            ex[j] = acc;
         }
+        s_gbase[d] = bin_off[d] + acc;
     }
     __syncthreads();
+
+    // ---- rank within the warp, in original order ----
+    // Lanes holding the same digit are found with one ballot per digit bit.
+    uint16_t *wh = s_whist + wid * R;
+    const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        int d = tid * PER + j;
-        if (d < R) s_gbase[d] = bin_off[d] + ex[j];
+    for (int k = 0; k < kSortItems; ++k) {
+        const bool valid = wbase + 32 * k + lane < n;
+        const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & MASK : (uint32_t)R;
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        uint32_t peers = valid ? vmask : ~vmask;
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+        const uint32_t pre = valid ? (uint32_t)wh[d] : 0u;
+        const uint32_t lower = __popc(peers & lt);
+        __syncwarp();
+        if (valid && lower == 0) wh[d] = (uint16_t)(pre + __popc(peers));
+        __syncwarp();
+        rank[k] = pre + lower;
+    }
+    __syncthreads();
+
+    // ---- per digit: exclusive prefix over the warps ----
+    for (int d = tid; d < R; d += kSortBlock) {
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t c = s_whist[w * R + d];
+            s_whist[w * R + d] = (uint16_t)r;
+            r += c;
+        }
     }
     __syncthreads();
 
@@ -298,7 +335,7 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__rest
 template <int RB, typename KeyT>
 static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, uint64_t n_max,
                              const uint64_t *n_dev, int end_bit, void *scratch, uint32_t *err, cudaStream_t s,
-                             int *passes_out) {
+                             int *passes_out, bool hist_ready) {
     constexpr int R = 1 << RB;
     const int passes = num_passes(end_bit, RB);
     const uint64_t tiles = (n_max + kSortTile - 1) / kSortTile;
@@ -307,7 +344,11 @@ static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
     uint32_t *counters = reinterpret_cast<uint32_t *>(base + (size_t)kMaxPasses * kHistStride * 4);
     uint32_t *lookback = reinterpret_cast<uint32_t *>(base + kSortHeader);
     *passes_out = passes;
-    cudaError_t e = cudaMemsetAsync(scratch, 0, kSortHeader + (size_t)passes * tiles * R * 4, s);
+    // with hist_ready the caller has already written every pass's exclusive
+    // bucket offsets into the histogram table: clear only counters and look-back
+    const size_t clear_from = hist_ready ? (size_t)kMaxPasses * kHistStride * 4 : 0;
+    cudaError_t e = cudaMemsetAsync(base + clear_from, 0,
+                                    kSortHeader - clear_from + (size_t)passes * tiles * R * 4, s);
     if (e != cudaSuccess || n_max == 0) return e;
 
     static bool attrs_set = false;
@@ -320,10 +361,12 @@ static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
         if (e != cudaSuccess) return e;
         attrs_set = true;
     }
-    uint64_t hblocks = std::min<uint64_t>((n_max + 255) / 256, 152 * 4);
-    sort_hist_kernel<RB, KeyT><<<(unsigned)hblocks, 256, (size_t)passes * R * 4, s>>>(keys, n_max, n_dev, passes,
-                                                                                        hist);
-    sort_hist_scan_kernel<RB><<<passes, 1024, 0, s>>>(hist);
+    if (!hist_ready) {
+        uint64_t hblocks = std::min<uint64_t>((n_max + 255) / 256, 152 * 4);
+        sort_hist_kernel<RB, KeyT><<<(unsigned)hblocks, 256, (size_t)passes * R * 4, s>>>(keys, n_max, n_dev,
+                                                                                            passes, hist);
+        sort_hist_scan_kernel<RB><<<passes, 1024, 0, s>>>(hist);
+    }
     KeyT *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     for (int p = 0; p < passes; ++p) {
@@ -339,13 +382,21 @@ static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
 template <typename KeyT>
 static cudaError_t sort_dispatch(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, uint64_t n_max,
                                  const uint64_t *n_dev, int end_bit, int digit_bits, void *scratch, uint32_t *err,
-                                 cudaStream_t s, int *passes_out) {
+                                 cudaStream_t s, int *passes_out, bool hist_ready) {
     if (end_bit > (int)(8 * sizeof(KeyT))) return cudaErrorInvalidValue;
     switch (digit_bits) {
-    case 8: return sort_impl<8>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out);
-    case 9: return sort_impl<9>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out);
-    case 10: return sort_impl<10>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out);
-    case 11: return sort_impl<11>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out);
+    case 8:
+        return sort_impl<8>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out,
+                            hist_ready);
+    case 9:
+        return sort_impl<9>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out,
+                            hist_ready);
+    case 10:
+        return sort_impl<10>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out,
+                             hist_ready);
+    case 11:
+        return sort_impl<11>(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, scratch, err, s, passes_out,
+                             hist_ready);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -354,14 +405,17 @@ cudaError_t sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint3
                        const uint64_t *n_dev, int end_bit, int digit_bits, void *scratch, uint32_t *err,
                        cudaStream_t s, int *passes_out) {
     return sort_dispatch(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, digit_bits, scratch, err, s,
-                         passes_out);
+                         passes_out, false);
 }
 
 cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t n_max,
                        const uint64_t *n_dev, int end_bit, int digit_bits, void *scratch, uint32_t *err,
-                       cudaStream_t s, int *passes_out) {
+                       cudaStream_t s, int *passes_out, bool hist_ready) {
     return sort_dispatch(keys, vals, keys_alt, vals_alt, n_max, n_dev, end_bit, digit_bits, scratch, err, s,
-                         passes_out);
+                         passes_out, hist_ready);
 }
+
+uint32_t *sort_hist_table(void *scratch) { return static_cast<uint32_t *>(scratch); }
+int sort_hist_stride() { return kHistStride; }
 
 }  // namespace qb
