@@ -111,6 +111,29 @@ CamDev to_cam(const qb_camera &c) {
     return d;
 }
 
+// A single frame is a set of one camera.
+TileSet frame_tileset(const qb_frame *f) {
+    TileSet ts;
+    std::memset(&ts, 0, sizeof(ts));
+    ts.n_cams = 1;
+    ts.total_tiles = (uint32_t)(f->tiles_x * f->tiles_y);
+    ts.cam[0].W = f->width;
+    ts.cam[0].H = f->height;
+    ts.cam[0].tiles_x = f->tiles_x;
+    ts.cam[0].tiles_y = f->tiles_y;
+    ts.cam[0].tile_base = 0;
+    ts.cam[0].pix_base = 0;
+    return ts;
+}
+
+CamSet frame_camset(const qb_camera &c) {
+    CamSet cs;
+    std::memset(&cs, 0, sizeof(cs));
+    cs.n_cams = 1;
+    cs.cam[0] = to_cam(c);
+    return cs;
+}
+
 qb_status check_frame(const qb_frame *f, Layout &L) {
     if (!f || !f->workspace) return fail(QB_ERR_INVALID_ARG, "frame is NULL or not initialised");
     if (!make_layout(f->n, f->width, f->height, f->pair_capacity, L))
@@ -246,7 +269,7 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     a.raw = scene->params_raw != 0;
     a.sh_vec4 = reinterpret_cast<uintptr_t>(scene->sh) % 16 == 0;
     a.quat_vec4 = reinterpret_cast<uintptr_t>(scene->quats) % 16 == 0;
-    a.cam = to_cam(*camera);
+    a.cams = frame_camset(*camera);
     a.mode = base_mode;
     a.clamp3s = (mode & QB_BIN_NO_CLAMP) == 0;
     a.xy = at<float2>(frame, L.xy);
@@ -256,9 +279,10 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     a.r3 = at<float>(frame, L.r3);
     a.meta = at<int>(frame, L.meta);
     a.counts = at<uint32_t>(frame, L.counts);
-    a.tiles_x = frame->tiles_x;
     a.tile_diff = nullptr;
     a.tile_single = nullptr;
+    std::memset(a.diff_off, 0, sizeof(a.diff_off));
+    std::memset(a.single_off, 0, sizeof(a.single_off));
     if (frame->sort_mode == QB_SORT_DEPTH_FIRST) {
         a.tile_diff = at<int>(frame, L.tile_diff);
         a.tile_single = at<int>(frame, L.tile_single);
@@ -309,8 +333,9 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         // per-tile counts -> ranges and the tile sort's bucket offsets
         const int tile_bits = frame->key_bits - kDepthBits;
         const int passes = tile_bits > 0 ? (tile_bits + frame->sort_digit_bits - 1) / frame->sort_digit_bits : 0;
-        QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), frame->tiles_x,
-                                 frame->tiles_y,
+        const uint32_t zero_off[1] = {0u};
+        QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), frame_tileset(frame),
+                                 zero_off, zero_off,
                                  at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
                                  sort_hist_stride(), frame->sort_digit_bits, passes, s));
         frame->reserved[1] = frame->sort_digit_bits;  // digit width the offsets were made for
@@ -330,6 +355,8 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     }
     EmitArgs a;
     a.n = frame->n;
+    a.n_per_cam = frame->n > 0 ? frame->n : 1;
+    a.ts = frame_tileset(frame);
     a.perm = perm;
     a.xy = at<float2>(frame, L.xy);
     a.box = at<float4>(frame, L.box);
@@ -344,9 +371,6 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     a.capacity = frame->pair_capacity;
     a.mode = frame->bin_mode & 0xff;
     a.clamp3s = (frame->bin_mode & QB_BIN_NO_CLAMP) == 0;
-    a.W = frame->width;
-    a.H = frame->height;
-    a.tiles_x = frame->tiles_x;
     a.err = err;
     if (depth_first)
         QB_CUDA(launch_emit<uint32_t>(a, at<uint32_t>(frame, L.keys0), s));
@@ -406,10 +430,10 @@ qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_strea
     a.xy = at<float2>(frame, L.xy);
     a.conic_o = at<float4>(frame, L.conic_o);
     a.rgbd = at<float4>(frame, L.rgbd);
-    a.W = frame->width;
-    a.H = frame->height;
-    a.tiles_x = frame->tiles_x;
-    a.tiles_y = frame->tiles_y;
+    a.ts = frame_tileset(frame);
+    a.queue = nullptr;
+    a.tiles_per_fetch = 1;
+    a.blocks_per_sm = 0;
     for (int c = 0; c < 3; ++c) a.bg[c] = bg ? bg[c] : 0.f;
     a.img = d_img;
     a.tfinal = at<float>(frame, L.tfinal);
@@ -444,10 +468,10 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
     b.xy = at<float2>(frame, L.xy);
     b.conic_o = at<float4>(frame, L.conic_o);
     b.rgbd = at<float4>(frame, L.rgbd);
-    b.W = frame->width;
-    b.H = frame->height;
-    b.tiles_x = frame->tiles_x;
-    b.tiles_y = frame->tiles_y;
+    b.ts = frame_tileset(frame);
+    b.queue = nullptr;
+    b.tiles_per_fetch = 1;
+    b.blocks_per_sm = 0;
     for (int c = 0; c < 3; ++c) b.bg[c] = bg ? bg[c] : 0.f;
     b.dL_dimg = d_dL_dimg;
     b.tfinal = at<float>(frame, L.tfinal);
@@ -462,7 +486,7 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
     p.opac = scene->opacities;
     p.sh = scene->sh;
     p.raw = scene->params_raw != 0;
-    p.cam = to_cam(*camera);
+    p.cams = frame_camset(*camera);
     p.meta = at<int>(frame, L.meta);
     p.g_screen = gscreen;
     p.gm = grads->means;

@@ -2,21 +2,24 @@
 // differentiable rasteriser (Sec. 4.1 states the rasteriser is differentiable;
 // the gradients below differentiate Eq. 2 and the Sec. 2 projection).
 //
-// K7: one 256-thread block per tile walks the tile list in reverse, from the
-// largest last-contributor position of its pixels down to 0.  Each pixel
-// recomputes alpha exactly as the forward did and the transmittance by
-// division, T_k = T_{k+1} / (1 - alpha_k), keeping the colour behind the
-// current entry, B_k = sum_{i>k} T_i alpha_i c_i + T_final bg:
+// K7: a 256-thread block per tile (one pixel per thread) walks the tile list
+// in reverse, from the largest last-contributor position of its pixels down
+// to 0.  Each pixel recomputes alpha exactly as the forward did and the
+// transmittance by division, T_k = T_{k+1} / (1 - alpha_k), keeping the colour
+// behind the current entry, B_k = sum_{i>k} T_i alpha_i c_i + T_final bg:
 //   dC/dc_k     = T_k alpha_k
 //   dC/dalpha_k = T_k c_k - B_k / (1 - alpha_k)
 // alpha = min(0.99, o G), G = exp(power): zero derivative where the cap binds.
-// Per Gaussian the 32 lanes of a warp are summed with shuffles and one lane
-// adds the 9 screen-space gradients atomically in float64: (mu_x, mu_y,
-// Sigma11, Sigma12, Sigma22, o, r, g, b), the covariance entries being the
-// well-conditioned parametrisation (dL/dLambda = -Sigma dL/dSigma Sigma).
+// The 9 per-Gaussian sums (mu_x, mu_y, Sigma11, Sigma12, Sigma22, o, r, g, b;
+// the covariance entries are the well-conditioned parametrisation, with
+// dL/dLambda = -Sigma dL/dSigma Sigma) are reduced over the warp by a
+// transpose-reduction (12 shuffles) that leaves one sum on each of 9 lanes,
+// which add them to float64 accumulators in parallel.  The same tile routine
+// serves one block per tile and a persistent kernel over several cameras.
 //
-// K8: one thread per Gaussian chains the (mu^2D, Sigma2D, o, colour) gradients
-// to means, (log-)scales, quaternions, opacity (logits) and SH.
+// K8: one thread per Gaussian chains the (mu^2D, Sigma2D, o, colour)
+// gradients of every camera of the set to means, (log-)scales, quaternions,
+// opacity (logits) and SH, summing over cameras in registers.
 #include "qb_kernels.cuh"
 #include "qb_project.cuh"
 
@@ -37,44 +40,72 @@ __device__ __forceinline__ double widen(float v) {
     return __longlong_as_double((long long)bits);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum g[0..8] over the warp and add the 9 totals to dst[0..8].  Each butterfly
+// step halves the vector every lane carries (9 -> 5 -> 3 -> 2 -> 1): lanes on
+// the lower side of a step keep the first half, those on the upper side the
+// second half.  Afterwards lane l (bit 0 clear) holds element
+// 5 b4 + 3 b3 + 2 b2 + b1 of the original vector, when that index is real.
+__device__ __forceinline__ void warp_reduce9_add(const float g[9], double *dst, int lane) {
+    const unsigned F = 0xffffffffu;
+    float w[5];
+    const bool u4 = lane & 16;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 5; ++i) {
+        const float lo = g[i], hi = (i + 5 < 9) ? g[i + 5] : 0.f;
+        w[i] = (u4 ? hi : lo) + __shfl_xor_sync(F, u4 ? lo : hi, 16);
+    }
+    float x[3];
+    const bool u3 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = w[i], hi = (i + 3 < 5) ? w[i + 3] : 0.f;
+        x[i] = (u3 ? hi : lo) + __shfl_xor_sync(F, u3 ? lo : hi, 8);
+    }
+    float y[2];
+    const bool u2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float lo = x[i], hi = (i + 2 < 3) ? x[i + 2] : 0.f;
+        y[i] = (u2 ? hi : lo) + __shfl_xor_sync(F, u2 ? lo : hi, 4);
+    }
+    const bool u1 = lane & 2;
+    float z = (u1 ? y[1] : y[0]) + __shfl_xor_sync(F, u1 ? y[0] : y[1], 2);
+    z += __shfl_xor_sync(F, z, 1);
+    const int ix = 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+    const int iw = 3 * ((lane >> 3) & 1) + ix;
+    const int iv = 5 * ((lane >> 4) & 1) + iw;
+    if (!(lane & 1) && ix < 3 && iw < 5 && iv < 9 && z != 0.f) atomicAdd(dst + iv, widen(z));
 }
 
-__global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
-    __shared__ uint32_t s_id[kBwdThreads];
-    __shared__ float4 s_xy[kBwdThreads];  // mu_x, mu_y, skip threshold
-    __shared__ float4 s_co[kBwdThreads];
-    __shared__ float4 s_rgb[kBwdThreads];
-    __shared__ int s_maxlast;
-
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+__device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile, int ci, uint32_t *s_id, float4 *s_m,
+                                                float4 *s_c, float4 *s_rgb, int *s_maxlast) {
+    const CamTile &C = a.ts.cam[ci];
+    const uint32_t lt = gtile - C.tile_base;
+    const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31;
     const int px = tx * kTile + (tid & (kTile - 1));
     const int py = ty * kTile + (tid >> kTileShift);
-    const bool inside = px < a.W && py < a.H;
+    const bool inside = px < C.W && py < C.H;
     const float pxf = (float)px, pyf = (float)py;
-    const size_t pix = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+    const size_t pix = (size_t)py * C.W + px, plane = (size_t)C.W * C.H;
 
     float T = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
     int last = 0;
     if (inside) {
-        T = a.tfinal[pix];
-        last = a.ncontrib[pix];
-        g0 = a.dL_dimg[pix];
-        g1 = a.dL_dimg[plane + pix];
-        g2 = a.dL_dimg[2 * plane + pix];
+        const float *dl = a.dL_dimg + 3 * C.pix_base;
+        T = a.tfinal[C.pix_base + pix];
+        last = a.ncontrib[C.pix_base + pix];
+        g0 = dl[pix];
+        g1 = dl[plane + pix];
+        g2 = dl[2 * plane + pix];
     }
     float B0 = T * a.bg[0], B1 = T * a.bg[1], B2 = T * a.bg[2];
-    if (tid == 0) s_maxlast = 0;
+    if (tid == 0) *s_maxlast = 0;
     __syncthreads();
-    if (last > 0) atomicMax(&s_maxlast, last);
+    if (last > 0) atomicMax(s_maxlast, last);
     __syncthreads();
-    const int maxlast = s_maxlast;
-    const uint32_t rstart = a.ranges[tile].x;
+    const int maxlast = *s_maxlast;
+    const uint32_t rstart = a.ranges[gtile].x;
 
     for (int end = maxlast; end > 0; end -= kBwdThreads) {
         const int cnt = min(kBwdThreads, end);
@@ -85,8 +116,8 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
             s_id[tid] = g;
             const float2 m = a.xy[g];
             const float4 co = a.conic_o[g];
-            s_xy[tid] = make_float4(m.x, m.y, skip_threshold(co.w), 0.f);
-            s_co[tid] = co;
+            s_m[tid] = make_float4(m.x, m.y, skip_threshold(co.w), co.w);
+            s_c[tid] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, 0.f);
             s_rgb[tid] = a.rgbd[g];
         }
         __syncthreads();
@@ -95,34 +126,35 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
             float gv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
             if (p < last) {
-                const float4 m = s_xy[j];
-                const float4 co = s_co[j];
+                const float4 m = s_m[j];
+                const float4 c = s_c[j];
                 const float dx = m.x - pxf, dy = m.y - pyf;
-                const float power = eval_power(co, dx, dy);
+                float A, Bt;
+                power_terms(c.x, c.y, dx, A, Bt);
+                const float power = power_from(A, Bt, c.z, dy);
                 if (power <= 0.f && power >= m.z) {
                     const float G = __expf(power);
-                    const float oG = __fmul_rn(co.w, G);
+                    const float oG = __fmul_rn(m.w, G);
                     const float alpha = fminf(kAlphaMax, oG);
                     if (alpha >= kAlphaMin) {
                         contrib = true;
-                        const float om = 1.f - alpha;
-                        T = T / om;  // transmittance in front of this entry
-                        const float4 c = s_rgb[j];
+                        const float inv = __frcp_rn(1.f - alpha);
+                        T = T * inv;  // transmittance in front of this entry
+                        const float4 rgb = s_rgb[j];
                         const float w = alpha * T;
                         gv[6] = w * g0;
                         gv[7] = w * g1;
                         gv[8] = w * g2;
-                        const float inv = 1.f / om;
-                        const float dalpha = g0 * (T * c.x - B0 * inv) + g1 * (T * c.y - B1 * inv) +
-                                             g2 * (T * c.z - B2 * inv);
-                        B0 = fmaf(w, c.x, B0);
-                        B1 = fmaf(w, c.y, B1);
-                        B2 = fmaf(w, c.z, B2);
+                        const float dalpha = g0 * (T * rgb.x - B0 * inv) + g1 * (T * rgb.y - B1 * inv) +
+                                             g2 * (T * rgb.z - B2 * inv);
+                        B0 = fmaf(w, rgb.x, B0);
+                        B1 = fmaf(w, rgb.y, B1);
+                        B2 = fmaf(w, rgb.z, B2);
                         if (oG < kAlphaMax) {
                             // power = -d^T Lambda d / 2 with Lambda = Sigma^-1 and u = Lambda d:
                             // dpower/dmu = -u, dpower/dSigma = u u^T / 2
                             const float dpower = dalpha * oG;
-                            const float ux = co.x * dx + co.y * dy, uy = co.y * dx + co.z * dy;
+                            const float ux = -2.f * c.x * dx - c.y * dy, uy = -c.y * dx - 2.f * c.z * dy;
                             gv[5] = G * dalpha;
                             gv[0] = -dpower * ux;
                             gv[1] = -dpower * uy;
@@ -133,26 +165,47 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
                     }
                 }
             }
-            if (__ballot_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int v = 0; v < 9; ++v) gv[v] = warp_sum(gv[v]);
-                if (lane == 0) {
-                    // float64 accumulation across warps and tiles: a large Gaussian
-                    // sums thousands of terms of both signs
-                    double *dst = a.g_screen + (size_t)s_id[j] * 9;
-#pragma unroll
-                    for (int v = 0; v < 9; ++v)
-                        if (gv[v] != 0.f) atomicAdd(dst + v, widen(gv[v]));
-                }
-            }
+            if (__ballot_sync(0xffffffffu, contrib)) warp_reduce9_add(gv, a.g_screen + (size_t)s_id[j] * 9, lane);
         }
     }
 }
 
+__global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
+    __shared__ uint32_t s_id[kBwdThreads];
+    __shared__ float4 s_m[kBwdThreads], s_c[kBwdThreads], s_rgb[kBwdThreads];
+    __shared__ int s_maxlast;
+    render_bwd_tile(a, blockIdx.x, 0, s_id, s_m, s_c, s_rgb, &s_maxlast);
+}
+
+__global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent_kernel(BwdArgs a) {
+    __shared__ uint32_t s_id[kBwdThreads];
+    __shared__ float4 s_m[kBwdThreads], s_c[kBwdThreads], s_rgb[kBwdThreads];
+    __shared__ int s_maxlast;
+    __shared__ uint32_t s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(a.queue, (uint32_t)a.tiles_per_fetch);
+        __syncthreads();
+        const uint32_t t0 = s_next;
+        __syncthreads();
+        if (t0 >= a.ts.total_tiles) break;
+        const uint32_t t1 = min(t0 + (uint32_t)a.tiles_per_fetch, a.ts.total_tiles);
+        for (uint32_t t = t0; t < t1; ++t)
+            render_bwd_tile(a, t, camera_of(a.ts, t), s_id, s_m, s_c, s_rgb, &s_maxlast);
+    }
+}
+
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
-    const int ntiles = a.tiles_x * a.tiles_y;
-    if (ntiles == 0) return cudaSuccess;
-    render_bwd_kernel<<<ntiles, kBwdThreads, 0, s>>>(a);
+    if (a.ts.total_tiles == 0) return cudaSuccess;
+    if (a.queue) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_persistent_kernel, kBwdThreads, 0);
+        if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
+        render_bwd_persistent_kernel<<<sms * (per_sm > 0 ? per_sm : 1), kBwdThreads, 0, s>>>(a);
+    } else {
+        render_bwd_kernel<<<a.ts.total_tiles, kBwdThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -160,133 +213,147 @@ template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PreBwdArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const int meta = a.meta[i];
-    if (!(meta & kMetaVisible)) return;
-    const CamDev &cam = a.cam;
+    constexpr int K = (DEG + 1) * (DEG + 1);
     const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
-    Proj p;
-    if (!project_gaussian(cam, m0, m1, m2, a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2],
-                          a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3], a.raw, p))
-        return;
-    const double *gsc = a.g_screen + (size_t)i * 9;
-    const float gmx = (float)gsc[0], gmy = (float)gsc[1], gop = (float)gsc[5];
-    const float grgb[3] = {(float)gsc[6], (float)gsc[7], (float)gsc[8]};
-    // gradient w.r.t. Sigma2D = [s11 s12; s12 s22] (s12 one parameter) as the
-    // full-matrix gradient H with dL = tr(H^T dSigma)
-    const float H00 = (float)gsc[2], H01 = 0.5f * (float)gsc[3], H11 = (float)gsc[4];
-    // Sigma2D = A A^T + 0.3 I  ->  dL/dA = 2 H A
-    float gA[6];
+    const float sc0 = a.scales[3 * i], sc1 = a.scales[3 * i + 1], sc2 = a.scales[3 * i + 2];
+    const float qw = a.quats[4 * i], qx = a.quats[4 * i + 1], qy = a.quats[4 * i + 2], qz = a.quats[4 * i + 3];
+    const float *sh = a.sh + (size_t)i * K * 3;
+    float gmean[3] = {0.f, 0.f, 0.f}, gsc[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
+    float gsh[K * 3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        gA[k] = 2.f * (H00 * p.A[k] + H01 * p.A[3 + k]);
-        gA[3 + k] = 2.f * (H01 * p.A[k] + H11 * p.A[3 + k]);
-    }
-    // A = M (R S), M = J W
-    const float *V = cam.V;
-    float M0[3], M1[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        M0[j] = fmaf(p.J00, V[j], p.J02 * V[8 + j]);
-        M1[j] = fmaf(p.J11, V[4 + j], p.J12 * V[8 + j]);
-    }
-    float gM0[3], gM1[3], gR[9], gs[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        gM0[j] = 0.f;
-        gM1[j] = 0.f;
+    for (int k = 0; k < K * 3; ++k) gsh[k] = 0.f;
+    bool any = false;
+    for (int cam = 0; cam < a.cams.n_cams; ++cam) {
+        const size_t rec = (size_t)cam * a.n + i;
+        const int meta = a.meta[rec];
+        if (!(meta & kMetaVisible)) continue;
+        const CamDev &cd = a.cams.cam[cam];
+        Proj p;
+        if (!project_gaussian(cd, m0, m1, m2, sc0, sc1, sc2, qw, qx, qy, qz, a.raw, p)) continue;
+        any = true;
+        const double *gsd = a.g_screen + rec * 9;
+        const float gmx = (float)gsd[0], gmy = (float)gsd[1];
+        gop += (float)gsd[5];
+        const float grgb[3] = {(float)gsd[6], (float)gsd[7], (float)gsd[8]};
+        // gradient w.r.t. Sigma2D = [s11 s12; s12 s22] (s12 one parameter) as the
+        // full-matrix gradient H with dL = tr(H^T dSigma)
+        const float H00 = (float)gsd[2], H01 = 0.5f * (float)gsd[3], H11 = (float)gsd[4];
+        // Sigma2D = A A^T + 0.3 I  ->  dL/dA = 2 H A
+        float gA[6];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float rs = p.R[3 * j + k] * p.s[k];
-            gM0[j] += gA[k] * rs;
-            gM1[j] += gA[3 + k] * rs;
-            const float grs = M0[j] * gA[k] + M1[j] * gA[3 + k];
-            gR[3 * j + k] = grs * p.s[k];
-            gs[k] += grs * p.R[3 * j + k];
+            gA[k] = 2.f * (H00 * p.A[k] + H01 * p.A[3 + k]);
+            gA[3 + k] = 2.f * (H01 * p.A[k] + H11 * p.A[3 + k]);
+        }
+        // A = M (R S), M = J W
+        const float *V = cd.V;
+        float M0[3], M1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            M0[j] = fmaf(p.J00, V[j], p.J02 * V[8 + j]);
+            M1[j] = fmaf(p.J11, V[4 + j], p.J12 * V[8 + j]);
+        }
+        float gM0[3], gM1[3], gR[9];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gM0[j] = 0.f;
+            gM1[j] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float rs = p.R[3 * j + k] * p.s[k];
+                gM0[j] += gA[k] * rs;
+                gM1[j] += gA[3 + k] * rs;
+                const float grs = M0[j] * gA[k] + M1[j] * gA[3 + k];
+                gR[3 * j + k] = grs * p.s[k];
+                gsc[k] += (a.raw ? p.s[k] : 1.f) * grs * p.R[3 * j + k];
+            }
+        }
+        float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gJ00 += gM0[j] * V[j];
+            gJ02 += gM0[j] * V[8 + j];
+            gJ11 += gM1[j] * V[4 + j];
+            gJ12 += gM1[j] * V[8 + j];
+        }
+        // J(t) and mu^2D(t) -> t
+        const float tz = p.tz, tzi = 1.f / tz, tzi2 = tzi * tzi;
+        float gtx = gmx * cd.fx * tzi, gty = gmy * cd.fy * tzi;
+        float gtz = -(gmx * cd.fx * p.tx + gmy * cd.fy * p.ty) * tzi2;
+        gtz += -(gJ00 * cd.fx + gJ11 * cd.fy) * tzi2;
+        if (p.clx) {
+            gtz += -gJ02 * p.J02 * tzi;  // J02 = -fx L / tz
+        } else {
+            gtx += -gJ02 * cd.fx * tzi2;
+            gtz += gJ02 * 2.f * cd.fx * p.tx * tzi2 * tzi;
+        }
+        if (p.cly) {
+            gtz += -gJ12 * p.J12 * tzi;
+        } else {
+            gty += -gJ12 * cd.fy * tzi2;
+            gtz += gJ12 * 2.f * cd.fy * p.ty * tzi2 * tzi;
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gmean[j] += V[j] * gtx + V[4 + j] * gty + V[8 + j] * gtz;
+
+        // rotation of the normalised quaternion -> quaternion
+        const float w = p.qn[0], x = p.qn[1], y = p.qn[2], z = p.qn[3];
+        const float gw = gR[1] * (-2.f * z) + gR[2] * (2.f * y) + gR[3] * (2.f * z) + gR[5] * (-2.f * x) +
+                         gR[6] * (-2.f * y) + gR[7] * (2.f * x);
+        const float gx = gR[1] * (2.f * y) + gR[2] * (2.f * z) + gR[3] * (2.f * y) + gR[4] * (-4.f * x) +
+                         gR[5] * (-2.f * w) + gR[6] * (2.f * z) + gR[7] * (2.f * w) + gR[8] * (-4.f * x);
+        const float gy = gR[0] * (-4.f * y) + gR[1] * (2.f * x) + gR[2] * (2.f * w) + gR[3] * (2.f * x) +
+                         gR[5] * (2.f * z) + gR[6] * (-2.f * w) + gR[7] * (2.f * z) + gR[8] * (-4.f * y);
+        const float gz = gR[0] * (-4.f * z) + gR[1] * (-2.f * w) + gR[2] * (2.f * x) + gR[3] * (2.f * w) +
+                         gR[4] * (-4.f * z) + gR[5] * (2.f * y) + gR[6] * (2.f * x) + gR[7] * (2.f * y);
+        const float dot = gw * w + gx * x + gy * y + gz * z;
+        const float iq = 1.f / p.qnorm;
+        gq[0] += (gw - w * dot) * iq;
+        gq[1] += (gx - x * dot) * iq;
+        gq[2] += (gy - y * dot) * iq;
+        gq[3] += (gz - z * dot) * iq;
+
+        // colour from SH
+        const float vx = m0 - cd.campos[0], vy = m1 - cd.campos[1], vz = m2 - cd.campos[2];
+        const float vn = sqrtf(vx * vx + vy * vy + vz * vz), ivn = 1.f / vn;
+        const float dx = vx * ivn, dy = vy * ivn, dz = vz * ivn;
+        float Y[16];
+        sh_eval<DEG>(dx, dy, dz, Y);
+        float gcol[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gcol[ch] = (meta >> (kMetaClampShift + ch)) & 1 ? 0.f : grgb[ch];
+        float wsh[16];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            gsh[3 * k] += Y[k] * gcol[0];
+            gsh[3 * k + 1] += Y[k] * gcol[1];
+            gsh[3 * k + 2] += Y[k] * gcol[2];
+            wsh[k] = sh[3 * k] * gcol[0] + sh[3 * k + 1] * gcol[1] + sh[3 * k + 2] * gcol[2];
+        }
+        if (DEG > 0) {
+            float ddx, ddy, ddz;
+            sh_grad<DEG>(dx, dy, dz, wsh, ddx, ddy, ddz);
+            const float r = ddx * dx + ddy * dy + ddz * dz;
+            gmean[0] += (ddx - r * dx) * ivn;
+            gmean[1] += (ddy - r * dy) * ivn;
+            gmean[2] += (ddz - r * dz) * ivn;
         }
     }
-    float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        gJ00 += gM0[j] * V[j];
-        gJ02 += gM0[j] * V[8 + j];
-        gJ11 += gM1[j] * V[4 + j];
-        gJ12 += gM1[j] * V[8 + j];
-    }
-    // J(t) and mu^2D(t) -> t
-    const float tz = p.tz, tzi = 1.f / tz, tzi2 = tzi * tzi;
-    float gtx = gmx * cam.fx * tzi, gty = gmy * cam.fy * tzi;
-    float gtz = -(gmx * cam.fx * p.tx + gmy * cam.fy * p.ty) * tzi2;
-    gtz += -(gJ00 * cam.fx + gJ11 * cam.fy) * tzi2;
-    if (p.clx) {
-        gtz += -gJ02 * p.J02 * tzi;  // J02 = -fx L / tz
-    } else {
-        gtx += -gJ02 * cam.fx * tzi2;
-        gtz += gJ02 * 2.f * cam.fx * p.tx * tzi2 * tzi;
-    }
-    if (p.cly) {
-        gtz += -gJ12 * p.J12 * tzi;
-    } else {
-        gty += -gJ12 * cam.fy * tzi2;
-        gtz += gJ12 * 2.f * cam.fy * p.ty * tzi2 * tzi;
-    }
-    float gmean[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gmean[j] = V[j] * gtx + V[4 + j] * gty + V[8 + j] * gtz;
-
-    // rotation of the normalised quaternion -> quaternion
-    const float w = p.qn[0], x = p.qn[1], y = p.qn[2], z = p.qn[3];
-    float gw = gR[1] * (-2.f * z) + gR[2] * (2.f * y) + gR[3] * (2.f * z) + gR[5] * (-2.f * x) +
-               gR[6] * (-2.f * y) + gR[7] * (2.f * x);
-    float gx = gR[1] * (2.f * y) + gR[2] * (2.f * z) + gR[3] * (2.f * y) + gR[4] * (-4.f * x) +
-               gR[5] * (-2.f * w) + gR[6] * (2.f * z) + gR[7] * (2.f * w) + gR[8] * (-4.f * x);
-    float gy = gR[0] * (-4.f * y) + gR[1] * (2.f * x) + gR[2] * (2.f * w) + gR[3] * (2.f * x) +
-               gR[5] * (2.f * z) + gR[6] * (-2.f * w) + gR[7] * (2.f * z) + gR[8] * (-4.f * y);
-    float gz = gR[0] * (-4.f * z) + gR[1] * (-2.f * w) + gR[2] * (2.f * x) + gR[3] * (2.f * w) +
-               gR[4] * (-4.f * z) + gR[5] * (2.f * y) + gR[6] * (2.f * x) + gR[7] * (2.f * y);
-    const float dot = gw * w + gx * x + gy * y + gz * z;
-    const float iq = 1.f / p.qnorm;
-    a.gq[4 * i] += (gw - w * dot) * iq;
-    a.gq[4 * i + 1] += (gx - x * dot) * iq;
-    a.gq[4 * i + 2] += (gy - y * dot) * iq;
-    a.gq[4 * i + 3] += (gz - z * dot) * iq;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a.gs[3 * i + k] += a.raw ? gs[k] * p.s[k] : gs[k];
-
-    // opacity
+    if (!any) return;
+    // opacity: o = sigmoid(logit) when raw
     const float ov = a.opac[i];
     const float o = a.raw ? 1.f / (1.f + expf(-ov)) : ov;
     a.go[i] += a.raw ? gop * o * (1.f - o) : gop;
-
-    // colour from SH
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    const float vx = m0 - cam.campos[0], vy = m1 - cam.campos[1], vz = m2 - cam.campos[2];
-    const float vn = sqrtf(vx * vx + vy * vy + vz * vz), ivn = 1.f / vn;
-    const float dx = vx * ivn, dy = vy * ivn, dz = vz * ivn;
-    float Y[16];
-    sh_eval<DEG>(dx, dy, dz, Y);
-    float gcol[3];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) gcol[ch] = (meta >> (kMetaClampShift + ch)) & 1 ? 0.f : grgb[ch];
-    const float *sh = a.sh + (size_t)i * K * 3;
-    float *gsh = a.gsh + (size_t)i * K * 3;
-    float wsh[16];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        gsh[3 * k] += Y[k] * gcol[0];
-        gsh[3 * k + 1] += Y[k] * gcol[1];
-        gsh[3 * k + 2] += Y[k] * gcol[2];
-        wsh[k] = sh[3 * k] * gcol[0] + sh[3 * k + 1] * gcol[1] + sh[3 * k + 2] * gcol[2];
-    }
-    if (DEG > 0) {
-        float ddx, ddy, ddz;
-        sh_grad<DEG>(dx, dy, dz, wsh, ddx, ddy, ddz);
-        const float r = ddx * dx + ddy * dy + ddz * dz;
-        gmean[0] += (ddx - r * dx) * ivn;
-        gmean[1] += (ddy - r * dy) * ivn;
-        gmean[2] += (ddz - r * dz) * ivn;
+    for (int j = 0; j < 3; ++j) {
+        a.gm[3 * i + j] += gmean[j];
+        a.gs[3 * i + j] += gsc[j];
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) a.gm[3 * i + j] += gmean[j];
+    for (int j = 0; j < 4; ++j) a.gq[4 * i + j] += gq[j];
+    float *gshp = a.gsh + (size_t)i * K * 3;
+#pragma unroll
+    for (int k = 0; k < K * 3; ++k) gshp[k] += gsh[k];
 }
 
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s) {

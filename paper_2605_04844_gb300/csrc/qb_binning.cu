@@ -168,6 +168,8 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
     __shared__ float s_inv[kEmitWarps][kSegPerWarp];
     __shared__ uint32_t s_gid[kEmitWarps][32];
     __shared__ uint32_t s_dbits[kEmitWarps][32];
+    __shared__ uint32_t s_tbase[kEmitWarps][32];  // first global tile of the owner's camera
+    __shared__ uint32_t s_tx[kEmitWarps][32];     // tiles per row of the owner's camera
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t P = *a.n_pairs;
     const uint64_t warp_id = (uint64_t)blockIdx.x * kEmitWarps + wid;
@@ -197,7 +199,6 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
     int64_t j0 = lo;
 
     const uint32_t le_mask = lanemask_le();
-    const uint32_t tx_n = (uint32_t)a.tiles_x;
     int32_t done_to = 0;  // chunk positions [0, done_to) written
     while (done_to < L && j0 < a.n) {
         const int64_t j = j0 + lane;
@@ -212,14 +213,17 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
         QSeg seg[7];
         int ns = 0;
         bool columns = false;
-        uint32_t dbits = 0;
+        uint32_t dbits = 0, tbase = 0, tx_n = 1;
         if (relevant) {
+            const CamTile &cam = a.ts.cam[gid / (uint32_t)a.n_per_cam];
+            tbase = cam.tile_base;
+            tx_n = (uint32_t)cam.tiles_x;
             const float2 xy = a.xy[gid];
             const int meta = a.meta[gid];
             dbits = __float_as_uint(a.rgbd[gid].w) & 0x7fffffffu;
             Rect r[4];
-            box_rects(xy.x, xy.y, a.box[gid], a.r3[gid], (meta & kMetaOrient) != 0, a.mode, a.clamp3s, a.W, a.H,
-                      r);
+            box_rects(xy.x, xy.y, a.box[gid], a.r3[gid], (meta & kMetaOrient) != 0, a.mode, a.clamp3s, cam.W,
+                      cam.H, r);
             QPass qp;
             if (qpass_setup(r, qp)) {
                 ns = qpass_segments(qp, seg);
@@ -229,6 +233,8 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
         __syncwarp();
         s_gid[wid][lane] = gid;
         s_dbits[wid][lane] = dbits;
+        s_tbase[wid][lane] = tbase;
+        s_tx[wid][lane] = tx_n;
         const int sincl = warp_incl_scan(ns);
         const int sbase = sincl - ns;
         const int nseg = __shfl_sync(0xffffffffu, sincl, 31);
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
                 const uint32_t u = (geo >> 16) + (uint32_t)r;
                 const bool cols = (ln >> 24) & 1u;
                 const uint32_t owner = (ln >> 16) & 0xffu;
-                const uint32_t tile = (cols ? u : line) * tx_n + (cols ? line : u);
+                const uint32_t tile = s_tbase[wid][owner] + (cols ? u : line) * s_tx[wid][owner] + (cols ? line : u);
                 keys[C + p] = make_key<KeyT>(tile, s_dbits[wid][owner]);
                 a.vals[C + p] = s_gid[wid][owner];
             }
@@ -303,10 +309,11 @@ __global__ void __launch_bounds__(256) emit_naive_kernel(EmitArgs a, KeyT *__res
     const float2 xy = a.xy[gid];
     const int meta = a.meta[gid];
     const uint32_t dbits = __float_as_uint(a.rgbd[gid].w) & 0x7fffffffu;
+    const CamTile &cam = a.ts.cam[gid / (uint32_t)a.n_per_cam];
     Rect r[4];
-    box_rects(xy.x, xy.y, a.box[gid], a.r3[gid], (meta & kMetaOrient) != 0, a.mode, a.clamp3s, a.W, a.H, r);
+    box_rects(xy.x, xy.y, a.box[gid], a.r3[gid], (meta & kMetaOrient) != 0, a.mode, a.clamp3s, cam.W, cam.H, r);
     uint32_t k = 0;
-    const uint32_t tx_n = (uint32_t)a.tiles_x;
+    const uint32_t tx_n = (uint32_t)cam.tiles_x;
     for (int q = 0; q < 4; ++q) {
         if (rect_empty(r[q])) continue;
         for (int ty = r[q].y0; ty <= r[q].y1; ++ty)
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(256) emit_naive_kernel(EmitArgs a, KeyT *__res
                 bool seen = false;
                 for (int p = 0; p < q; ++p) seen |= in_rect(r[p], tx, ty);
                 if (seen || k >= c) continue;
-                keys[off + k] = make_key<KeyT>((uint32_t)ty * tx_n + (uint32_t)tx, dbits);
+                keys[off + k] = make_key<KeyT>(cam.tile_base + (uint32_t)ty * tx_n + (uint32_t)tx, dbits);
                 a.vals[off + k] = gid;
                 ++k;
             }
@@ -369,42 +376,53 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
     return cudaGetLastError();
 }
 
-// Per-tile pair counts from the difference array written by the preprocess:
-// a 2D prefix sum plus the single-tile counts gives each tile's count; an exclusive scan over tile ids
-// gives the ranges of the tile-sorted pairs; the counts summed per digit give
-// the exclusive bucket offsets of every pass of the tile sort.  One block.
-__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, int tx, int ty, uint2 *ranges,
-                                                         uint32_t *hist, int hist_stride, int rb, int passes) {
+// Per-tile pair counts from the difference arrays written by the preprocess:
+// for every camera of the set a 2D prefix sum plus the single-tile counts
+// gives each tile's count; an exclusive scan over the global tile ids gives
+// the ranges of the tile-sorted pairs; the counts summed per digit give the
+// exclusive bucket offsets of every pass of the tile sort.  One block.
+__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, TileSet ts, TileOffsets off,
+                                                         uint2 *ranges, uint32_t *hist, int hist_stride, int rb,
+                                                         int passes) {
     extern __shared__ uint32_t sh_hist[];  // passes * 2^rb
     const int R = 1 << rb;
-    const int stride = tx + 1;
     for (int j = threadIdx.x; j < passes * R; j += blockDim.x) sh_hist[j] = 0u;
-    for (int y = threadIdx.x; y < ty; y += blockDim.x) {
-        int run = 0;
-        for (int x = 0; x < tx; ++x) {
-            run += D[y * stride + x];
-            D[y * stride + x] = run;
+    for (int c = 0; c < ts.n_cams; ++c) {
+        const int tx = ts.cam[c].tiles_x, ty = ts.cam[c].tiles_y, stride = tx + 1;
+        int *Dc = D + off.diff[c];
+        const int *Sc = single + off.single[c];
+        for (int y = threadIdx.x; y < ty; y += blockDim.x) {
+            int run = 0;
+            for (int x = 0; x < tx; ++x) {
+                run += Dc[y * stride + x];
+                Dc[y * stride + x] = run;
+            }
         }
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < tx; x += blockDim.x) {
-        int run = 0;
-        for (int y = 0; y < ty; ++y) {
-            run += D[y * stride + x];
-            D[y * stride + x] = run + single[y * tx + x];
+        __syncthreads();
+        for (int x = threadIdx.x; x < tx; x += blockDim.x) {
+            int run = 0;
+            for (int y = 0; y < ty; ++y) {
+                run += Dc[y * stride + x];
+                Dc[y * stride + x] = run + Sc[y * tx + x];
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // exclusive scan of the counts over tile ids, each thread a contiguous chunk
-    const int ntiles = tx * ty;
+    // exclusive scan of the counts over global tile ids, each thread a chunk
+    const int ntiles = (int)ts.total_tiles;
     const int per = (ntiles + blockDim.x - 1) / blockDim.x;
     const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
+    auto count_of = [&](int t) -> uint32_t {
+        const int c = camera_of(ts, (uint32_t)t);
+        const int lt = t - (int)ts.cam[c].tile_base, tx = ts.cam[c].tiles_x;
+        return (uint32_t)D[off.diff[c] + (lt / tx) * (tx + 1) + lt % tx];
+    };
     uint32_t local = 0;
-    for (int t = t0; t < t1; ++t) local += (uint32_t)D[(t / tx) * stride + t % tx];
+    for (int t = t0; t < t1; ++t) local += count_of(t);
     uint32_t total;
     uint32_t run = block_incl_scan<uint32_t>(local, &total) - local;
     for (int t = t0; t < t1; ++t) {
-        const uint32_t c = (uint32_t)D[(t / tx) * stride + t % tx];
+        const uint32_t c = count_of(t);
         ranges[t] = c ? make_uint2(run, run + c) : make_uint2(0u, 0u);  // [0,0) for an empty tile
         run += c;
         for (int p = 0; p < passes; ++p) atomicAdd(&sh_hist[p * R + ((t >> (p * rb)) & (R - 1))], c);
@@ -425,11 +443,17 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
     }
 }
 
-cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, int tiles_x, int tiles_y, uint2 *ranges,
-                             uint32_t *hist, int hist_stride, int digit_bits, int passes, cudaStream_t s) {
+cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileSet &ts, const uint32_t *diff_off,
+                             const uint32_t *single_off, uint2 *ranges, uint32_t *hist, int hist_stride,
+                             int digit_bits, int passes, cudaStream_t s) {
+    TileOffsets off;
+    for (int c = 0; c < kMaxGroupCams; ++c) {
+        off.diff[c] = c < ts.n_cams ? diff_off[c] : 0u;
+        off.single[c] = c < ts.n_cams ? single_off[c] : 0u;
+    }
     const size_t smem = (size_t)passes * ((size_t)1 << digit_bits) * 4;
-    tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, tiles_x, tiles_y, ranges, hist, hist_stride,
-                                           digit_bits, passes);
+    tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, ts, off, ranges, hist, hist_stride, digit_bits,
+                                           passes);
     return cudaGetLastError();
 }
 

@@ -79,13 +79,20 @@ int sort_hist_stride();
 // them first never changes a decision of that test.
 __device__ __forceinline__ float skip_threshold(float o) { return -logf(255.0f * o) - 1e-3f; }
 
-// Exponent of the 2D Gaussian at offset (dx, dy) = mu^2D - pixel:
-// -(a dx^2 + c dy^2)/2 - b dx dy.  The operation sequence is spelled out with
-// intrinsics so the forward and backward kernels take identical decisions.
-__device__ __forceinline__ float eval_power(const float4 &co, float dx, float dy) {
-    const float dxdx = __fmul_rn(dx, dx), dydy = __fmul_rn(dy, dy), dxdy = __fmul_rn(dx, dy);
-    const float s = fmaf(co.x, dxdx, __fmul_rn(co.z, dydy));
-    return fmaf(-0.5f, s, -__fmul_rn(co.y, dxdy));
+// Exponent of the 2D Gaussian at offset (dx, dy) = mu^2D - pixel,
+// -(a dx^2 + 2 b dx dy + c dy^2) / 2, evaluated as a quadratic in dy:
+//   A + dy (B + cc dy),  A = ca dx^2, B = cb dx,
+// with (ca, cb, cc) = (-a/2, -b, -c/2), exact rescalings of the conic.  A and
+// B depend on the pixel column only.  The operation sequence is spelled out
+// with intrinsics so the forward and backward kernels take identical
+// decisions.
+__device__ __forceinline__ void power_terms(float ca, float cb, float dx, float &A, float &B) {
+    A = __fmul_rn(__fmul_rn(ca, dx), dx);
+    B = __fmul_rn(cb, dx);
+}
+
+__device__ __forceinline__ float power_from(float A, float B, float cc, float dy) {
+    return __fmaf_rn(dy, __fmaf_rn(cc, dy, B), A);
 }
 
 struct Rect {

@@ -14,7 +14,9 @@ template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const CamDev &cam = a.cam;
+    const int ci = blockIdx.y;  // camera of this grid row
+    const CamDev &cam = a.cams.cam[ci];
+    const size_t o = (size_t)ci * a.n + i;  // output record
     const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
     Proj p;
     float4 q4;
@@ -31,8 +33,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
         ok = p.o >= kAlphaMin;  // no pixel of this Gaussian reaches alpha_min
     }
     if (!ok) {
-        a.counts[i] = 0u;
-        a.meta[i] = 0;
+        a.counts[o] = 0u;
+        a.meta[o] = 0;
         return;
     }
     BoxTerms bt = box_terms(p);
@@ -89,40 +91,42 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
         const int ns = qpass_segments(qp, seg);
         // QPass count: the lines of each run of equal intervals times its length
         for (int q = 0; q < ns; ++q) cnt += (uint32_t)(seg[q].nl * seg[q].len);
+        const int tiles_x = (cam.W + kTile - 1) >> kTileShift;
         if (a.tile_diff && cnt == 1u) {
             // one tile (the common case): count it directly
-            const int t = qp.columns ? seg[0].lo * a.tiles_x + seg[0].s0 : seg[0].s0 * a.tiles_x + seg[0].lo;
-            atomicAdd(a.tile_single + t, 1);
+            const int t = qp.columns ? seg[0].lo * tiles_x + seg[0].s0 : seg[0].s0 * tiles_x + seg[0].lo;
+            atomicAdd(a.tile_single + a.single_off[ci] + t, 1);
         } else if (a.tile_diff) {
             // per-tile pair counts as a 2D difference array: +1/-1 at the corners
             // of every rectangle of the Gaussian's tile set
-            const int stride = a.tiles_x + 1;
+            const int stride = tiles_x + 1;
+            int *D = a.tile_diff + a.diff_off[ci];
             for (int q = 0; q < ns; ++q) {
                 const int l0 = seg[q].s0, l1 = seg[q].s0 + seg[q].nl - 1;
                 const int u0 = seg[q].lo, u1 = seg[q].lo + seg[q].len - 1;
                 const int x0 = qp.columns ? l0 : u0, x1 = qp.columns ? l1 : u1;
                 const int y0 = qp.columns ? u0 : l0, y1 = qp.columns ? u1 : l1;
-                atomicAdd(a.tile_diff + y0 * stride + x0, 1);
-                atomicAdd(a.tile_diff + y0 * stride + x1 + 1, -1);
-                atomicAdd(a.tile_diff + (y1 + 1) * stride + x0, -1);
-                atomicAdd(a.tile_diff + (y1 + 1) * stride + x1 + 1, 1);
+                atomicAdd(D + y0 * stride + x0, 1);
+                atomicAdd(D + y0 * stride + x1 + 1, -1);
+                atomicAdd(D + (y1 + 1) * stride + x0, -1);
+                atomicAdd(D + (y1 + 1) * stride + x1 + 1, 1);
             }
         }
     }
     if (a.mode == QB_BIN_QUADBOX_NAIVE) cnt = naive_count(rects);  // the same set, counted the naive way
 
-    a.xy[i] = make_float2(p.mx, p.my);
-    a.conic_o[i] = make_float4(p.a, p.b, p.c, p.o);
-    a.rgbd[i] = make_float4(rgb[0], rgb[1], rgb[2], p.tz);
-    a.box[i] = bt.box;
-    a.r3[i] = bt.r3;
-    a.meta[i] = meta;
-    a.counts[i] = cnt;
+    a.xy[o] = make_float2(p.mx, p.my);
+    a.conic_o[o] = make_float4(p.a, p.b, p.c, p.o);
+    a.rgbd[o] = make_float4(rgb[0], rgb[1], rgb[2], p.tz);
+    a.box[o] = bt.box;
+    a.r3[o] = bt.r3;
+    a.meta[o] = meta;
+    a.counts[o] = cnt;
 }
 
 cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    dim3 grid((a.n + 255) / 256), block(256);
+    dim3 grid((a.n + 255) / 256, a.cams.n_cams), block(256);
     switch (deg) {
     case 0: preprocess_kernel<0><<<grid, block, 0, s>>>(a); break;
     case 1: preprocess_kernel<1><<<grid, block, 0, s>>>(a); break;
