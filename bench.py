@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--digit-bits", type=int, default=None)
     ap.add_argument("--sort-mode", default="depth_first", choices=["depth_first", "full_key"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched comparison")
+    ap.add_argument("--batch-cams", type=int, default=64)
+    ap.add_argument("--batch-n", type=int, default=1_000_000)
     ap.add_argument("--out", default=None, help="also write the JSON line here")
     return ap.parse_args()
 
@@ -366,6 +369,117 @@ def roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
     return out
 
 
+def run_batch(args, dev):
+    """64 cameras of uneven resolution around a 1M-Gaussian scene: one
+    graph-captured qb_render_batch (fwd, and fwd+bwd with an L1 loss against a
+    random target) versus 64 separate single-frame launch sequences."""
+    import numpy as np
+    import torch
+
+    from paper_2605_04844_gb300 import _native as N
+    from paper_2605_04844_gb300 import autotune
+    from paper_2605_04844_gb300 import rasterizer as R
+    from paper_2605_04844_gb300 import synth
+
+    scene_np, cams = synth.config5(args.batch_n, args.batch_cams)
+    sd = {k: (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v) for k, v in scene_np.items()}
+    s = R.scene_struct(sd)
+    ca = R.camera_array(cams)
+    b = R.calibrated_batch(sd, cams, group=16)
+    tune = autotune.tune_batch(b, sd, cams)
+    t = tune["tune"]
+    stream = torch.cuda.current_stream(dev)
+    target = torch.rand(b.images.shape, device=dev, generator=torch.Generator(dev).manual_seed(2005))
+    npix = sum(w * h for w, h in zip(b.widths, b.heights))
+    grads = {k: torch.zeros_like(sd[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    gs = N.QbSceneGrads()
+    gs.means, gs.scales, gs.quats = grads["means"].data_ptr(), grads["scales"].data_ptr(), grads["quats"].data_ptr()
+    gs.opacities, gs.sh = grads["opacities"].data_ptr(), grads["sh"].data_ptr()
+    dL = torch.empty_like(b.images)
+
+    def fwd():
+        b.render(s, ca, "quadbox", t)
+
+    def fwd_bwd():
+        b.render(s, ca, "quadbox", t)
+        torch.sub(b.images, target, out=dL)
+        dL.sign_().mul_(1.0 / (3 * npix))
+        for g in grads.values():
+            g.zero_()
+        b.backward(s, ca, dL, gs)
+
+    fwd_bwd()  # first calls outside capture
+    torch.cuda.synchronize()
+    pairs = b.check()
+    graphs = {}
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    for name, fn in (("fwd", fwd), ("fwd_bwd", fwd_bwd)):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            b.stream = side
+            with torch.cuda.graph(g, stream=side):
+                fn()
+        b.stream = None
+        graphs[name] = g
+    torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / steps
+
+    steps = max(3, min(args.steps, 10))
+    g_fwd = timed(graphs["fwd"].replay, steps, 2)
+    g_fb = timed(graphs["fwd_bwd"].replay, steps, 2)
+    b.check()
+
+    # the same cameras as separate single-frame launch sequences
+    frames = {}
+    for c in cams:  # one frame per resolution, grown to the largest camera's pairs
+        key = (c["width"], c["height"])
+        _, frames[key] = R.forward(sd, c, "quadbox", frame=frames.get(key), digit_bits=t["sort_digit_bits"])
+    for fr in frames.values():
+        fr.set_tuning(render_batch=t["render_batch"])
+    imgs = {key: torch.empty((3, key[1], key[0]), device=dev) for key in frames}
+    dls = {key: torch.full((3, key[1], key[0]), 1.0 / (3 * npix), device=dev) for key in frames}
+    cam_structs = [R.camera_struct(c) for c in cams]
+
+    def separate(with_bwd):
+        for c, cs in zip(cams, cam_structs):
+            key = (c["width"], c["height"])
+            fr = frames[key]
+            fr.preprocess(s, cs, "quadbox")
+            fr.bin_emit(sync=False)
+            fr.sort()
+            fr.render(None, imgs[key])
+            if with_bwd:
+                N.qb_render_bwd(fr.frame, s, cs, None, dls[key], gs, None)
+
+    sep_fwd = timed(lambda: separate(False), max(2, steps // 2), 1)
+    sep_fb = timed(lambda: separate(True), max(2, steps // 2), 1)
+    for fr in frames.values():
+        fr.check()
+    K = len(cams)
+    return {"workload": f"{args.batch_n} Gaussians, {K} cameras on a radius-8 sphere, resolutions from "
+                        "800x800/1264x832/1600x900/1920x1080, groups of 16 cameras",
+            "pairs_per_group": pairs, "tune": t,
+            "graph_fwd_ms": round(g_fwd, 3), "graph_fwd_bwd_ms": round(g_fb, 3),
+            "separate_fwd_ms": round(sep_fwd, 3), "separate_fwd_bwd_ms": round(sep_fb, 3),
+            "graph_fwd_cams_per_s": round(K * 1000.0 / g_fwd, 1),
+            "graph_fwd_bwd_cams_per_s": round(K * 1000.0 / g_fb, 1),
+            "speedup_fwd": round(sep_fwd / g_fwd, 3), "speedup_fwd_bwd": round(sep_fb / g_fb, 3)}
+
+
 # FP32 operations per evaluated (pixel, Gaussian) entry of render_kernel:
 # dx, dy (2), power (3 mul + 2 fma + 1 neg-mul = 6), compare (1), exp (2:
 # scale + ex2), o*G (1), min (1), compare (1), 1-alpha (1), T*(1-alpha) (1),
@@ -462,6 +576,9 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and not args.no_batch:
+        import torch
+        res["batch64"] = run_batch(args, torch.device("cuda", local_rank))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             from paper_2605_04844_gb300 import synth

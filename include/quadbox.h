@@ -252,6 +252,78 @@ qb_status qb_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_keys_alt
                         uint64_t n, int32_t end_bit, int32_t digit_bits, void *d_scratch,
                         size_t scratch_bytes, int32_t *result_in_alt, qb_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* Many cameras of one scene in one launch sequence (batched rendering).     */
+/* ------------------------------------------------------------------------ */
+
+#define QB_MAX_CAMERAS 256
+#define QB_GROUP_MAX 16
+
+/* Launch parameters of the batched path (picked by the autotuner).
+ *  tiles_per_fetch  tiles a persistent render block takes from the global
+ *                   tile-work queue at a time (1..8)
+ *  render_batch     Gaussians staged per shared-memory batch (64, 128, 256)
+ *  sort_digit_bits  radix digit width of the tile sort (8..11)
+ *  blocks_per_sm    persistent render blocks per SM (0: as many as fit) */
+typedef struct {
+    int32_t tiles_per_fetch;
+    int32_t render_batch;
+    int32_t sort_digit_bits;
+    int32_t blocks_per_sm;
+} qb_tune;
+
+/* Batch state.  Cameras are processed in groups of `group` (<= QB_GROUP_MAX);
+ * within a group all stages run as one kernel each over every camera, and
+ * the render is one persistent kernel fed by a global queue over all the
+ * group's tiles, so cameras of uneven resolution balance.  Images are packed
+ * in one float buffer: camera k's planar [3][height][width] image starts at
+ * float offset image_offset[k].  pair_capacity bounds the Gaussian-tile pairs
+ * of one group (<= 2^30).  Fields are read-only for the caller. */
+typedef struct {
+    int32_t n, n_cams, group, n_groups;
+    uint64_t pair_capacity;
+    void *workspace;
+    size_t workspace_bytes;
+    int32_t widths[QB_MAX_CAMERAS], heights[QB_MAX_CAMERAS];
+    uint64_t image_offset[QB_MAX_CAMERAS];
+    uint64_t total_floats;  /* size of the packed image buffer in floats */
+    int32_t sh_degree, bin_mode, stage, sorted_tile_bits;
+    int32_t reserved[8];
+} qb_batch;
+
+/* Bytes of device workspace for a batch (0 for invalid sizes). */
+size_t qb_batch_workspace_bytes(int32_t n, int32_t n_cams, const int32_t *widths, const int32_t *heights,
+                                int32_t group, uint64_t pair_capacity);
+
+/* Binds a caller-owned, 256-byte aligned device workspace to *batch. */
+qb_status qb_batch_init(qb_batch *batch, int32_t n, int32_t n_cams, const int32_t *widths, const int32_t *heights,
+                        int32_t group, uint64_t pair_capacity, void *d_workspace, size_t workspace_bytes,
+                        qb_stream_t stream);
+
+/* Forward of every camera of the batch:
+ * per group, one preprocess over all (camera, Gaussian) records, depth
+ * order, scan, per-tile counts, QPass emit with global tile ids, tile sort
+ * and one persistent render over the group's tiles.  cams: host array of
+ * n_cams cameras whose sizes match qb_batch_init; tune: host, NULL for
+ * defaults; d_images: device floats, total_floats of them.  No host
+ * synchronisation and no allocation, so a call can be captured in a CUDA
+ * graph (the cameras and tuning are then fixed in the graph); make one call
+ * outside capture first.  Pair-capacity overflow is flagged on the device and
+ * reported by qb_batch_check. */
+qb_status qb_render_batch(qb_batch *batch, const qb_scene *scene, const qb_camera *cams, int32_t mode,
+                          const qb_tune *tune, const float *bg, float *d_images, qb_stream_t stream);
+
+/* Backward of the last qb_render_batch (same scene, cameras and bg):
+ * accumulates into grads the gradient of sum(d_dL_dimages * images).
+ * d_dL_dimages is packed like the images.  Capturable like the forward. */
+qb_status qb_render_batch_bwd(qb_batch *batch, const qb_scene *scene, const qb_camera *cams, const float *bg,
+                              const float *d_dL_dimages, qb_scene_grads *grads, qb_stream_t stream);
+
+/* Synchronises and reports overflow or time-outs of the last batch calls;
+ * if pairs_out (host, n_groups entries) is non-NULL it receives the pairs
+ * of every group. */
+qb_status qb_batch_check(qb_batch *batch, uint64_t *pairs_out, qb_stream_t stream);
+
 /* The same sort for callers that may not allocate device memory (no
  * counterpart in the paper).  Some callers cannot call cudaMalloc: a plug-in
  * whose host application owns all device memory, a render loop that must not

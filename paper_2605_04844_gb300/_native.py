@@ -59,6 +59,23 @@ class QbFrame(ctypes.Structure):
                 ("sorted_in_alt", c_i32), ("sort_mode", c_i32), ("depth_in_alt", c_i32), ("reserved", c_i32 * 3)]
 
 
+QB_MAX_CAMERAS = 256
+QB_GROUP_MAX = 16
+
+
+class QbTune(ctypes.Structure):
+    _fields_ = [("tiles_per_fetch", c_i32), ("render_batch", c_i32), ("sort_digit_bits", c_i32),
+                ("blocks_per_sm", c_i32)]
+
+
+class QbBatch(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("n_cams", c_i32), ("group", c_i32), ("n_groups", c_i32), ("pair_capacity", c_u64),
+                ("workspace", c_vp), ("workspace_bytes", c_size), ("widths", c_i32 * QB_MAX_CAMERAS),
+                ("heights", c_i32 * QB_MAX_CAMERAS), ("image_offset", c_u64 * QB_MAX_CAMERAS),
+                ("total_floats", c_u64), ("sh_degree", c_i32), ("bin_mode", c_i32), ("stage", c_i32),
+                ("sorted_tile_bits", c_i32), ("reserved", c_i32 * 8)]
+
+
 class QbFrameArrays(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("xy", "conic_o", "rgbd", "box", "r3", "meta", "counts", "offsets",
                                           "keys", "tile_keys", "vals", "depth_order", "ranges", "t_final",
@@ -85,6 +102,14 @@ _SIGS = [
     ("qb_sort_scratch_bytes", c_size, [c_u64, c_i32, c_i32]),
     ("qb_sort_pairs", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, c_i32, c_vp, c_size,
                               ctypes.POINTER(c_i32), c_vp]),
+    ("qb_batch_workspace_bytes", c_size, [c_i32, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), c_i32, c_u64]),
+    ("qb_batch_init", c_i32, [ctypes.POINTER(QbBatch), c_i32, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
+                              c_i32, c_u64, c_vp, c_size, c_vp]),
+    ("qb_render_batch", c_i32, [ctypes.POINTER(QbBatch), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera), c_i32,
+                                ctypes.POINTER(QbTune), ctypes.POINTER(c_f), c_vp, c_vp]),
+    ("qb_render_batch_bwd", c_i32, [ctypes.POINTER(QbBatch), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera),
+                                    ctypes.POINTER(c_f), c_vp, ctypes.POINTER(QbSceneGrads), c_vp]),
+    ("qb_batch_check", c_i32, [ctypes.POINTER(QbBatch), ctypes.POINTER(c_u64), c_vp]),
     ("qb_sort_pairs_noalloc_max_scratch", c_size, []),
     ("qb_sort_pairs_noalloc", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, c_i32, ctypes.POINTER(c_i32), c_vp]),
 ]
@@ -209,3 +234,42 @@ def qb_sort_pairs_noalloc(keys, vals, keys_alt, vals_alt, n, end_bit, digit_bits
     check(load().qb_sort_pairs_noalloc(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt), n, end_bit, digit_bits,
                                        ctypes.byref(alt), stream_handle(stream)))
     return bool(alt.value)
+
+
+# ---------------------------------------------------------------------------
+# Batched multi-camera rendering
+# ---------------------------------------------------------------------------
+
+def _int_array(vals):
+    arr = (c_i32 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def qb_batch_workspace_bytes(n, widths, heights, group, pair_capacity) -> int:
+    return int(load().qb_batch_workspace_bytes(n, len(widths), _int_array(widths), _int_array(heights), group,
+                                               pair_capacity))
+
+
+def qb_batch_init(batch: QbBatch, n, widths, heights, group, pair_capacity, workspace, stream=None):
+    check(load().qb_batch_init(ctypes.byref(batch), n, len(widths), _int_array(widths), _int_array(heights), group,
+                               pair_capacity, ptr(workspace), workspace.numel() * workspace.element_size(),
+                               stream_handle(stream)))
+
+
+def qb_render_batch(batch: QbBatch, scene: QbScene, cams_array, mode: int, tune: QbTune, bg, images, stream=None):
+    check(load().qb_render_batch(ctypes.byref(batch), ctypes.byref(scene), cams_array, mode,
+                                 ctypes.byref(tune) if tune is not None else None, _bg(bg), ptr(images),
+                                 stream_handle(stream)))
+
+
+def qb_render_batch_bwd(batch: QbBatch, scene: QbScene, cams_array, bg, dL_dimages, grads: QbSceneGrads,
+                        stream=None):
+    check(load().qb_render_batch_bwd(ctypes.byref(batch), ctypes.byref(scene), cams_array, _bg(bg),
+                                     ptr(dL_dimages), ctypes.byref(grads), stream_handle(stream)))
+
+
+def qb_batch_check(batch: QbBatch, stream=None):
+    """Returns the pairs of every group (synchronises)."""
+    out = (c_u64 * max(1, batch.n_groups))()
+    check(load().qb_batch_check(ctypes.byref(batch), out, stream_handle(stream)))
+    return [int(out[i]) for i in range(batch.n_groups)]

@@ -77,3 +77,39 @@ def tune_frame(scene, cam, mode="quadbox", reps=5, use_cache=True):
         db[key] = res
         _save(db)
     return dict(res, cached=False)
+
+
+BATCH_SPACE = {
+    "sort_digit_bits": (8, 10, 11),
+    "render_batch": (64, 128, 256),
+    "tiles_per_fetch": (1, 2, 4),
+    "blocks_per_sm": (0, 2, 4),
+}
+
+
+def tune_batch(batch, scene, cams, mode="quadbox", reps=2, use_cache=True):
+    """Coordinate descent over the batched path's launch parameters (sort
+    digit width, staging batch depth, tiles per queue fetch, persistent
+    blocks per SM), timing qb_render_batch on the caller's scene and cameras."""
+    key = (f"{torch.cuda.get_device_name()}|batch|n={batch.n}|cams={batch.n_cams}|group={batch.group}|"
+           f"{'-'.join(f'{w}x{h}' for w, h in zip(batch.widths, batch.heights))[:200]}|{mode}")
+    db = _load() if use_cache else {}
+    if key in db:
+        return dict(db[key], cached=True)
+    scene_s, cams_arr = R.scene_struct(scene), R.camera_array(cams)
+    best = {"sort_digit_bits": 8, "render_batch": 128, "tiles_per_fetch": 2, "blocks_per_sm": 0}
+    timings = {}
+    for name, values in BATCH_SPACE.items():
+        res = {}
+        for v in values:
+            cand = dict(best, **{name: v})
+            batch.render(scene_s, cams_arr, mode, cand)  # warm
+            res[v] = _time(lambda: batch.render(scene_s, cams_arr, mode, cand), reps)
+        best[name] = min(res, key=res.get)
+        timings[name] = {str(k): round(t, 3) for k, t in res.items()}
+    batch.check()
+    out = {"tune": best, "ms": timings}
+    if use_cache:
+        db[key] = out
+        _save(db)
+    return dict(out, cached=False)

@@ -337,7 +337,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), frame_tileset(frame),
                                  zero_off, zero_off,
                                  at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
-                                 sort_hist_stride(), frame->sort_digit_bits, passes, s));
+                                 sort_hist_stride(), frame->sort_digit_bits, passes, frame->pair_capacity, s));
         frame->reserved[1] = frame->sort_digit_bits;  // digit width the offsets were made for
     }
     frame->n_pairs = UINT64_MAX;

@@ -355,7 +355,7 @@ __device__ __forceinline__ uint32_t tile_of(KeyT k) {
 template <typename KeyT>
 __global__ void ranges_kernel(const KeyT *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges,
                               uint32_t ntiles) {
-    uint64_t n = n_dev ? min(*n_dev, n_max) : n_max;
+    uint64_t n = n_dev ? (*n_dev > n_max ? 0 : *n_dev) : n_max;  // overflow (flagged by the emit): no pairs
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t tile = tile_of(keys[idx]);
@@ -383,7 +383,7 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
 // exclusive bucket offsets of every pass of the tile sort.  One block.
 __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, TileSet ts, TileOffsets off,
                                                          uint2 *ranges, uint32_t *hist, int hist_stride, int rb,
-                                                         int passes) {
+                                                         int passes, uint64_t capacity) {
     extern __shared__ uint32_t sh_hist[];  // passes * 2^rb
     const int R = 1 << rb;
     for (int j = threadIdx.x; j < passes * R; j += blockDim.x) sh_hist[j] = 0u;
@@ -417,12 +417,17 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
         const int lt = t - (int)ts.cam[c].tile_base, tx = ts.cam[c].tiles_x;
         return (uint32_t)D[off.diff[c] + (lt / tx) * (tx + 1) + lt % tx];
     };
-    uint32_t local = 0;
-    for (int t = t0; t < t1; ++t) local += count_of(t);
+    uint64_t local64 = 0;
+    for (int t = t0; t < t1; ++t) local64 += count_of(t);
+    uint64_t total64;
+    block_incl_scan<uint64_t>(local64, &total64);
+    // more pairs than the buffers hold (the emit flags it): every tile empty
+    const bool over = total64 > capacity;
+    uint32_t local = over ? 0u : (uint32_t)local64;
     uint32_t total;
     uint32_t run = block_incl_scan<uint32_t>(local, &total) - local;
     for (int t = t0; t < t1; ++t) {
-        const uint32_t c = count_of(t);
+        const uint32_t c = over ? 0u : count_of(t);
         ranges[t] = c ? make_uint2(run, run + c) : make_uint2(0u, 0u);  // [0,0) for an empty tile
         run += c;
         for (int p = 0; p < passes; ++p) atomicAdd(&sh_hist[p * R + ((t >> (p * rb)) & (R - 1))], c);
@@ -445,7 +450,7 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
 
 cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileSet &ts, const uint32_t *diff_off,
                              const uint32_t *single_off, uint2 *ranges, uint32_t *hist, int hist_stride,
-                             int digit_bits, int passes, cudaStream_t s) {
+                             int digit_bits, int passes, uint64_t capacity, cudaStream_t s) {
     TileOffsets off;
     for (int c = 0; c < kMaxGroupCams; ++c) {
         off.diff[c] = c < ts.n_cams ? diff_off[c] : 0u;
@@ -453,7 +458,7 @@ cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileS
     }
     const size_t smem = (size_t)passes * ((size_t)1 << digit_bits) * 4;
     tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, ts, off, ranges, hist, hist_stride, digit_bits,
-                                           passes);
+                                           passes, capacity);
     return cudaGetLastError();
 }
 

@@ -135,7 +135,7 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
                           cudaStream_t s);
 cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileSet &ts, const uint32_t *diff_off,
                              const uint32_t *single_off, uint2 *ranges, uint32_t *hist, int hist_stride,
-                             int digit_bits, int passes, cudaStream_t s);
+                             int digit_bits, int passes, uint64_t capacity, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs &a, int batch, cudaStream_t s);
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s);

@@ -40,6 +40,14 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Elements to sort: the device count when given, treated as zero when it
+// exceeds the buffers (an overflow the emit has already flagged).
+__device__ __forceinline__ uint64_t device_count(const uint64_t *n_dev, uint64_t n_max) {
+    if (!n_dev) return n_max;
+    const uint64_t n = *n_dev;
+    return n > n_max ? 0 : n;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -91,7 +99,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const KeyT *__restrict__
     extern __shared__ uint32_t sh[];
     for (int j = threadIdx.x; j < passes * R; j += blockDim.x) sh[j] = 0u;
     __syncthreads();
-    const uint64_t n = n_dev ? min(*n_dev, n_max) : n_max;
+    const uint64_t n = device_count(n_dev, n_max);
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const KeyT k = keys[idx];
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__rest
     for (int j = tid; j < R; j += kSortBlock) s_bcount[j] = 0u;
     __syncthreads();
     const uint32_t tile = s_tile;
-    const uint64_t n = n_dev ? min(*n_dev, n_max) : n_max;
+    const uint64_t n = device_count(n_dev, n_max);
     const uint64_t tbase = (uint64_t)tile * kSortTile;
     if (tbase >= n) return;  // block-uniform
 

@@ -217,3 +217,91 @@ class QuadBoxRasterize(torch.autograd.Function):
 
 def rasterize(means, scales, quats, opacities, sh, cam, mode="quadbox", bg=None):
     return QuadBoxRasterize.apply(means, scales, quats, opacities, sh, cam, mode, bg)
+
+
+def camera_array(cams):
+    """A C array of qb_camera structs for the batch entry points."""
+    arr = (N.QbCamera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera_struct(c)
+    return arr
+
+
+def tune_struct(tune=None) -> N.QbTune:
+    t = N.QbTune()
+    d = {"tiles_per_fetch": 2, "render_batch": 128, "sort_digit_bits": 8, "blocks_per_sm": 0}
+    d.update(tune or {})
+    t.tiles_per_fetch, t.render_batch = int(d["tiles_per_fetch"]), int(d["render_batch"])
+    t.sort_digit_bits, t.blocks_per_sm = int(d["sort_digit_bits"]), int(d["blocks_per_sm"])
+    return t
+
+
+class Batch:
+    """Many cameras of one scene rendered with the batched entry points.
+
+    Cameras are processed in groups of `group`; `pair_capacity` bounds the
+    Gaussian-tile pairs of one group (see calibrate()).  Images are packed in
+    one buffer; image(k) is camera k's [3, H, W] view."""
+
+    def __init__(self, n, cams, group=16, pair_capacity=None, device="cuda", stream=None):
+        self.n = int(n)
+        self.widths = [int(c["width"]) for c in cams]
+        self.heights = [int(c["height"]) for c in cams]
+        self.group = int(min(group, N.QB_GROUP_MAX, len(cams)))
+        if pair_capacity is None:
+            tiles = max(((w + 15) // 16) * ((h + 15) // 16) for w, h in zip(self.widths, self.heights))
+            pair_capacity = min(2 ** 30, self.group * max(8 * self.n, 4 * tiles))
+        self.pair_capacity = int(pair_capacity)
+        self.device = device
+        self.stream = stream
+        nbytes = N.qb_batch_workspace_bytes(self.n, self.widths, self.heights, self.group, self.pair_capacity)
+        if nbytes == 0:
+            raise ValueError("invalid batch sizes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.workspace.data_ptr()) % 256
+        self.ws = self.workspace[off:off + nbytes]
+        self.batch = N.QbBatch()
+        N.qb_batch_init(self.batch, self.n, self.widths, self.heights, self.group, self.pair_capacity, self.ws, stream)
+        self.images = torch.empty(int(self.batch.total_floats), dtype=torch.float32, device=device)
+
+    @property
+    def n_cams(self):
+        return len(self.widths)
+
+    def image(self, k, buf=None):
+        buf = self.images if buf is None else buf
+        o = int(self.batch.image_offset[k])
+        H, W = self.heights[k], self.widths[k]
+        return buf[o:o + 3 * H * W].view(3, H, W)
+
+    def render(self, scene_s: N.QbScene, cams_arr, mode="quadbox", tune=None, bg=None):
+        N.qb_render_batch(self.batch, scene_s, cams_arr, mode_id(mode), tune_struct(tune), bg, self.images,
+                          self.stream)
+        return self.images
+
+    def backward(self, scene_s: N.QbScene, cams_arr, dL_dimages, grads: N.QbSceneGrads, bg=None):
+        N.qb_render_batch_bwd(self.batch, scene_s, cams_arr, bg, dL_dimages, grads, self.stream)
+
+    def check(self):
+        return N.qb_batch_check(self.batch, self.stream)
+
+
+def calibrated_batch(scene, cams, mode="quadbox", group=16, headroom=1.1, tune=None):
+    """A Batch whose pair capacity fits this scene and these cameras: one
+    render with a generous capacity measures the pairs of every group."""
+    scene_s, cams_arr = scene_struct(scene), camera_array(cams)
+    n = scene_s.n
+    probe = Batch(n, cams, group, pair_capacity=None)
+    while True:
+        probe.render(scene_s, cams_arr, mode, tune)
+        try:
+            pairs = probe.check()
+            break
+        except N.QbCapacityError:
+            cap = min(2 ** 30, probe.pair_capacity * 4)
+            if cap == probe.pair_capacity:
+                raise
+            probe = Batch(n, cams, group, pair_capacity=cap)
+    cap = min(2 ** 30, int(max(pairs) * headroom) + 4096)
+    del probe
+    return Batch(n, cams, group, pair_capacity=cap)
