@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--digit-bits", type=int, default=None)
-    ap.add_argument("--sort-mode", default="depth_first", choices=["depth_first", "full_key"])
+    ap.add_argument("--sort-mode", default="depth_first", choices=["depth_first", "full_key", "chunked"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched comparison")
     ap.add_argument("--batch-cams", type=int, default=64)
@@ -143,10 +143,11 @@ def run_ours(args, rank, world, local_rank):
         cap = int(fr.n_pairs * 1.1) + 4096
         frames[mode] = R.Frame(n, W, H, cap)
         frames[mode].set_tuning(digit_bits=digit_bits, sort_mode=args.sort_mode)
-    # the same QuadBox frame with the other pair-ordering scheme, for comparison
-    other_mode = "full_key" if args.sort_mode == "depth_first" else "depth_first"
-    frames["quadbox_other"] = R.Frame(n, W, H, int(pairs["quadbox"] * 1.1) + 4096)
-    frames["quadbox_other"].set_tuning(digit_bits=8, sort_mode=other_mode)
+    # the same QuadBox frame with the other pair-ordering schemes, for comparison
+    other_modes = [m for m in ("depth_first", "chunked", "full_key") if m != args.sort_mode]
+    for m in other_modes:
+        frames["quadbox_" + m] = R.Frame(n, W, H, int(pairs["quadbox"] * 1.1) + 4096)
+        frames["quadbox_" + m].set_tuning(digit_bits=8, sort_mode=m)
     img = torch.empty((3, H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     grads = {k: torch.zeros_like(sd[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
@@ -173,8 +174,7 @@ def run_ours(args, rank, world, local_rank):
             N.qb_render_bwd(fr.frame, scene_s, cam_s, bg, dL, gs, None)
             ev[5].record(stream)
 
-    mode_of = {id(frames["quadbox"]): "quadbox", id(frames["aabb3s"]): "aabb3s",
-               id(frames["quadbox_other"]): "quadbox"}
+    mode_of = {id(fr): ("aabb3s" if name == "aabb3s" else "quadbox") for name, fr in frames.items()}
 
     def run_phase(mode, with_bwd, steps, warmup):
         fr = frames[mode]
@@ -187,7 +187,9 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(steps):
             flush.zero_()  # L2 flush between timed steps (outside the events)
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(nev)]
+            l0 = N.qb_kernel_launches()
             step(fr, with_bwd, evs)
+            launches[0] += N.qb_kernel_launches() - l0
             recs.append(evs)
         torch.cuda.synchronize()
         fr.check()
@@ -211,6 +213,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    launches = [0]  # kernels of the library launched inside the timed steps
     clocks = ClockSampler(local_rank)
     clocks.start()
     barrier()
@@ -220,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
     fb_ms, fb_stages = run_phase("quadbox", True, args.steps, args.warmup)
     afwd_ms, afwd_stages = run_phase("aabb3s", False, args.steps, args.warmup)
     afb_ms, afb_stages = run_phase("aabb3s", True, args.steps, args.warmup)
-    ofwd_ms, ofwd_stages = run_phase("quadbox_other", False, args.steps, args.warmup)
+    others = {m: run_phase("quadbox_" + m, False, args.steps, args.warmup) for m in other_modes}
     torch.cuda.synchronize()
     barrier()
     wall = time.time() - t_wall0
@@ -246,6 +249,7 @@ def run_ours(args, rank, world, local_rank):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        l0 = N.qb_kernel_launches()
         for k, v in pinned.items():
             sd[k].copy_(v, non_blocking=True)
         fr.preprocess(scene_s, cam_s, "quadbox")
@@ -257,6 +261,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e_times.append(e0.elapsed_time(e1))
+            launches[0] += N.qb_kernel_launches() - l0
     fr.check()
     e2e_ms = max_over_ranks(statistics.mean(e2e_times))
 
@@ -288,8 +293,8 @@ def run_ours(args, rank, world, local_rank):
                    "stage_ms": {k: round(v, 4) for k, v in afb_stages.items()}},
         "speedup_vs_aabb": {"fwd": round(afwd_ms / fwd_ms, 3), "fwd_bwd": round(afb_ms / fb_ms, 3),
                             "pair_ratio": round(pairs["aabb3s"] / max(P, 1), 3)},
-        "quadbox_" + other_mode: {"fwd_ms": round(ofwd_ms, 4),
-                                   "stage_ms": {k: round(v, 4) for k, v in ofwd_stages.items()}},
+        "quadbox_other_sort_modes": {m: {"fwd_ms": round(v[0], 4), "stage_ms": {k: round(x, 4) for k, x in v[1].items()}}
+                                     for m, v in others.items()},
         "paper_context": "paper: 1.85x FPS over 3DGS, mean over Mip-NeRF 360/DB/T&T on NVIDIA A100 (Table 1)",
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -297,15 +302,9 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": round(wall, 2),
     }
     result["roofline"] = roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode)
-    tile_bits = (((W + 15) // 16) * ((H + 15) // 16) - 1).bit_length()
-    if args.sort_mode == "depth_first":
-        per_fwd = 1 + (1 + 2 + 4) + 3 + 1 + 1 + -(-tile_bits // digit_bits) + 1
-        per_other = 1 + 3 + 1 + (2 + -(-(31 + tile_bits) // 8)) + 1 + 1
-    else:
-        per_fwd = 1 + 3 + 1 + (2 + -(-(31 + tile_bits) // digit_bits)) + 1 + 1
-        per_other = 1 + (1 + 2 + 4) + 3 + 1 + 1 + -(-tile_bits // 8) + 1
-    # fwd and fwd+bwd phases for both binnings, the comparison phase, the e2e loop
-    result["gpu_launches"] = args.steps * (2 * per_fwd + 2 * (per_fwd + 2) + per_other + per_fwd)
+    # counted by the library at each launch, inside the timed steps of every
+    # phase and of the end-to-end loop
+    result["gpu_launches"] = int(launches[0])
     if tune:
         result["autotune"] = tune
     return result
@@ -315,15 +314,22 @@ def stage_bytes(P, n, W, H, digit_bits, sort_mode):
     """Algorithmic HBM bytes of the emit and sort stages of one frame."""
     tiles = ((W + 15) // 16) * ((H + 15) // 16)
     tile_bits = (tiles - 1).bit_length()
+    if sort_mode == "chunked":
+        # no sort stage: per Gaussian the depth keys (read 20 B, write 8 B), the
+        # depth sort of n 4-byte keys + values (4 passes, 16 B each), the scan
+        # (read 8 B, write 4 B) and the segment record (64 B) read twice (count
+        # and placement); per pair one 4 B value written at its final position
+        return 0, n * (28 + 4 * 16 + 12 + 2 * 64) + 4 * P
     if sort_mode == "depth_first":
-        # tile sort: each pass reads and writes a 4 B key and a 4 B value (the
-        # bucket offsets and ranges come from the per-tile counts)
-        passes = -(-tile_bits // digit_bits)
-        sort_bytes = P * passes * 16
         # emit: depth keys (read 20 B, write 8 B per Gaussian), depth sort of n
-        # 4-byte keys + values (4 passes), scan (read 8 B, write 4 B), box record
-        # read (48 B), pairs written (8 B each)
-        emit_bytes = n * (28 + 4 * 16 + 4 + 12 + 48) + 8 * P
+        # 4-byte keys + values (4 passes, 16 B each), scan (read 8 B, write
+        # 4 B), segment record read (16 B), pairs written (8 B each)
+        passes = -(-tile_bits // digit_bits)
+        emit_bytes = n * (28 + 4 * 16 + 12 + 16) + 8 * P
+        # sort: the tile-id histogram (4 B per pair), 16 B per pair for every
+        # pass but the last (read and write key and value), 12 B for the last
+        # (it writes values only; the ranges come from the per-tile counts)
+        sort_bytes = P * (4 + 16 * max(0, passes - 1) + (12 if passes >= 1 else 0))
     else:
         passes = -(-(31 + tile_bits) // digit_bits)
         sort_bytes = P * (8 + passes * 24 + 8) + tiles * 8
@@ -341,6 +347,15 @@ def roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sort_bytes, emit_bytes = stage_bytes(P, n, W, H, digit_bits, sort_mode)
+    pre_bytes = n * PREPROCESS_BYTES
+    stage_kernel = {"preprocess": "preprocess_kernel", "render": "render_kernel",
+                    "emit": {"chunked": "depth sort + chunk_count/scan + chunk_emit_kernel",
+                             "depth_first": "depth sort + scan + emit_warp_kernel",
+                             "full_key": "emit_warp_kernel"}[sort_mode],
+                    "sort": {"chunked": "(none: pairs placed by the emit)",
+                             "depth_first": "tile_count_kernel + onesweep_kernel (tile-sort passes)",
+                             "full_key": "onesweep_kernel (+hist, ranges)"}[sort_mode]}
+    hbm_bytes = {"preprocess": pre_bytes, "emit": emit_bytes, "sort": sort_bytes}
     dom = max(fwd_stages, key=lambda k: fwd_stages[k])
     out = {}
     if dom == "render" and n_eval:
@@ -353,18 +368,17 @@ def roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median sampled clock)",
                "evaluations": n_eval}
     else:
-        ach = sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9
-        out = {"kernel": "onesweep_kernel (tile sort passes)" if sort_mode == "depth_first"
-               else "onesweep_kernel (+hist, ranges)", "bound": "hbm", "achieved": round(ach, 1),
+        ach = hbm_bytes[dom] / (fwd_stages[dom] * 1e-3) / 1e9
+        out = {"kernel": stage_kernel[dom], "bound": "hbm", "achieved": round(ach, 1),
                "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    # secondary: the HBM-bound stages
-    out["hbm_stages"] = {
-        "sort": {"GB/s": round(sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9, 1),
-                 "frac": round(sort_bytes / (fwd_stages["sort"] * 1e-3) / 1e9 / hbm, 4), "bytes": sort_bytes},
-        "emit": {"GB/s": round(emit_bytes / (fwd_stages["emit"] * 1e-3) / 1e9, 1),
-                 "frac": round(emit_bytes / (fwd_stages["emit"] * 1e-3) / 1e9 / hbm, 4), "bytes": emit_bytes},
-    }
+    # every HBM-bound stage
+    out["hbm_stages"] = {}
+    for st, b in hbm_bytes.items():
+        if b and fwd_stages.get(st, 0) > 1e-3:
+            gbs = b / (fwd_stages[st] * 1e-3) / 1e9
+            out["hbm_stages"][st] = {"kernel": stage_kernel[st], "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                                     "bytes": b}
     out["dominant_stage"] = dom
     return out
 
@@ -479,6 +493,11 @@ def run_batch(args, dev):
             "graph_fwd_bwd_cams_per_s": round(K * 1000.0 / g_fb, 1),
             "speedup_fwd": round(sep_fwd / g_fwd, 3), "speedup_fwd_bwd": round(sep_fb / g_fb, 3)}
 
+
+# Algorithmic bytes of the preprocess per Gaussian: read 44 B of parameters and
+# 192 B of SH coefficients (degree 3), write mu^2D 8, conic+o 16, colour+depth
+# 16, box 16, 3-sigma radius 4, meta 4, count 4 (68 B).
+PREPROCESS_BYTES = 236 + 68
 
 # FP32 operations per evaluated (pixel, Gaussian) entry of render_kernel:
 # dx, dy (2), power (3 mul + 2 fma + 1 neg-mul = 6), compare (1), exp (2:

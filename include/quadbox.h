@@ -69,14 +69,22 @@ typedef enum {
 } qb_bin_mode;
 #define QB_BIN_NO_CLAMP 0x100
 
-/* How qb_bin_emit/qb_sort order the pairs by (tile, depth, index).  Both give
+/* How qb_bin_emit/qb_sort order the pairs by (tile, depth, index).  All give
  * identical sorted values and ranges.
  *  DEPTH_FIRST  (default) sort the n Gaussians by (depth, index) once, emit
  *               each Gaussian's pairs in that order with 32-bit tile keys, then
- *               stable-sort the pairs on the tile bits only.
+ *               stable-sort the pairs on the tile bits only (the emit runs the
+ *               first digit pass itself).
  *  FULL_KEY     emit in index order with 64-bit keys (tile << 31) | depth
- *               bits and stable-sort on all 31 + tile bits (SortPairs, Sec. 2). */
-typedef enum { QB_SORT_DEPTH_FIRST = 0, QB_SORT_FULL_KEY = 1 } qb_sort_mode;
+ *               bits and stable-sort on all 31 + tile bits (SortPairs, Sec. 2).
+ *  CHUNKED      depth order as DEPTH_FIRST, then a counting placement instead
+ *               of radix passes: per chunk of 65536 depth-ordered pairs the
+ *               tile counts come from the QPass segments, their scan over the
+ *               chunks gives every (chunk, tile) its first output position, and
+ *               each pair is written once, at its final position.  Frames whose
+ *               per-tile tables do not fit shared memory (more than about
+ *               24000 tiles), and the QUADBOX_NAIVE mode, run DEPTH_FIRST. */
+typedef enum { QB_SORT_DEPTH_FIRST = 0, QB_SORT_FULL_KEY = 1, QB_SORT_CHUNKED = 2 } qb_sort_mode;
 
 /* Pinhole camera.  viewmat: row-major 4x4 world->view, last row (0,0,0,1);
  * view space looks down +z.  Pixel (px, py) has its centre at
@@ -141,6 +149,12 @@ typedef struct {
     int32_t sorted_in_alt;    /* internal: sorted pairs live in buffer 1    */
     int32_t sort_mode;        /* qb_sort_mode; set before qb_preprocess     */
     int32_t depth_in_alt;     /* internal: depth order lives in buffer 1    */
+    int32_t emit_fused;       /* DEPTH_FIRST: 1 = the emit performs the tile
+                                 sort's first digit pass (per-tile counts from
+                                 the preprocess); 0 (default) = plain emit, the
+                                 per-tile counts from a histogram of the
+                                 emitted tile ids in qb_sort; set before
+                                 qb_preprocess                               */
     int32_t reserved[3];      /* internal */
 } qb_frame;
 
@@ -158,8 +172,9 @@ typedef struct {
     uint32_t *offsets;  /* [n]     exclusive prefix of counts in emission order
                                    (index order, or depth order in DEPTH_FIRST) */
     uint64_t *keys;     /* [P]     FULL_KEY: (tile << 31) | depth bits, sorted after qb_sort */
-    uint32_t *tile_keys;/* [P]     DEPTH_FIRST: tile id, sorted after qb_sort */
-    uint32_t *vals;     /* [P]     Gaussian index                           */
+    uint32_t *tile_keys;/* [P]     DEPTH_FIRST: scratch of the tile sort; the sorted
+                                   tile ids are given by the ranges (qb_frame_tile_keys) */
+    uint32_t *vals;     /* [P]     Gaussian index, in sorted order after qb_sort */
     uint32_t *depth_order; /* [n]  DEPTH_FIRST: Gaussians by (depth, index) */
     uint32_t *ranges;   /* [tiles][2] [start, end) into keys/vals           */
     float *t_final;     /* [H][W]  transmittance after the last contributor */
@@ -176,6 +191,10 @@ const char *qb_last_error(void);
 /* Library version string. */
 const char *qb_version(void);
 
+/* Number of CUDA kernels the library has launched in this process (all
+ * threads, all devices), counted on the host at each launch. */
+uint64_t qb_kernel_launches(void);
+
 /* Bytes of device workspace for a frame of n Gaussians, a width x height
  * image and room for pair_capacity Gaussian-tile pairs (pair_capacity
  * <= 2^30).  Returns 0 for invalid sizes. */
@@ -190,6 +209,12 @@ qb_status qb_frame_init(qb_frame *frame, int32_t n, int32_t width, int32_t heigh
 
 /* Device pointers of the frame's internal arrays. */
 qb_status qb_frame_arrays_get(const qb_frame *frame, qb_frame_arrays *out);
+
+/* Writes the sorted pairs' tile ids (tile t at every position of its range)
+ * to d_out (device uint32 [n_out]) from the per-tile ranges, for inspection
+ * in either sort mode; positions >= n_out are skipped.  Errors: STATE before
+ * qb_sort, INVALID_ARG for a NULL d_out with n_out > 0. */
+qb_status qb_frame_tile_keys(const qb_frame *frame, uint32_t *d_out, uint64_t n_out, qb_stream_t stream);
 
 /* Synchronises the stream and reports device-side failures recorded in the
  * frame (CAPACITY, TIMEOUT); clears them. */
@@ -209,7 +234,11 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
  * tile counts, then one (key, value) pair per Gaussian-tile overlap with
  * key = (tile << 31) | float bits of the depth (FULL_KEY) or the tile id
  * (DEPTH_FIRST, after sorting the Gaussians by depth), value = Gaussian
- * index, written at the Gaussian's scan offset in emission order.
+ * index, in emission order (each Gaussian's pairs at its scan offset).  In
+ * DEPTH_FIRST the per-tile counts give the ranges here, and in the QPass
+ * modes the emit also performs the first digit pass of the tile sort, so the
+ * pairs leave it bucketed by their lowest tile digit rather than in emission
+ * order.
  * If n_pairs_out is non-NULL the host synchronises once to read P, stores it
  * in *n_pairs_out and frame->n_pairs, and returns CAPACITY (writing no pairs)
  * when P > pair_capacity.  With NULL nothing synchronises; an overflow is
@@ -217,8 +246,10 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
 qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream);
 
 /* Stage 3 (Sec. 2 "SortPairs"): stable LSD radix sort of the pairs with the
- * library's onesweep sort on the key bits [0, 31 + tile bits) (FULL_KEY) or
- * [0, tile bits) (DEPTH_FIRST), then the per-tile [start, end) ranges. */
+ * library's onesweep sort on the key bits [0, 31 + tile bits) (FULL_KEY),
+ * then the per-tile [start, end) ranges; or the remaining digit passes on
+ * the tile bits (DEPTH_FIRST), whose last pass writes only the values (in
+ * vals, sorted_in_alt = 0). */
 qb_status qb_sort(qb_frame *frame, qb_stream_t stream);
 
 /* Stage 4 (Sec. 2 "Render", Eq. 2): front-to-back compositing per pixel.

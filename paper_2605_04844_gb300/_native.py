@@ -56,7 +56,8 @@ class QbFrame(ctypes.Structure):
                 ("pair_capacity", c_u64), ("workspace", c_vp), ("workspace_bytes", c_size),
                 ("bin_mode", c_i32), ("sh_degree", c_i32), ("key_bits", c_i32), ("stage", c_i32),
                 ("n_pairs", c_u64), ("sort_digit_bits", c_i32), ("render_batch", c_i32),
-                ("sorted_in_alt", c_i32), ("sort_mode", c_i32), ("depth_in_alt", c_i32), ("reserved", c_i32 * 3)]
+                ("sorted_in_alt", c_i32), ("sort_mode", c_i32), ("depth_in_alt", c_i32), ("emit_fused", c_i32),
+                ("reserved", c_i32 * 3)]
 
 
 QB_MAX_CAMERAS = 256
@@ -88,10 +89,12 @@ _lib = None
 _SIGS = [
     ("qb_last_error", ctypes.c_char_p, []),
     ("qb_version", ctypes.c_char_p, []),
+    ("qb_kernel_launches", c_u64, []),
     ("qb_frame_workspace_bytes", c_size, [c_i32, c_i32, c_i32, c_u64]),
     ("qb_frame_init", c_i32, [ctypes.POINTER(QbFrame), c_i32, c_i32, c_i32, c_u64, c_vp, c_size, c_vp]),
     ("qb_frame_arrays_get", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbFrameArrays)]),
     ("qb_frame_check", c_i32, [ctypes.POINTER(QbFrame), c_vp]),
+    ("qb_frame_tile_keys", c_i32, [ctypes.POINTER(QbFrame), c_vp, c_u64, c_vp]),
     ("qb_preprocess", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera),
                               c_i32, c_vp]),
     ("qb_bin_emit", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(c_u64), c_vp]),
@@ -179,6 +182,15 @@ def qb_frame_arrays_get(frame: QbFrame) -> QbFrameArrays:
 
 def qb_frame_check(frame: QbFrame, stream=None):
     check(load().qb_frame_check(ctypes.byref(frame), stream_handle(stream)))
+
+
+def qb_kernel_launches() -> int:
+    return int(load().qb_kernel_launches())
+
+
+def qb_frame_tile_keys(frame: QbFrame, out, stream=None):
+    """Fills the device uint32/int32 tensor `out` (its length bounds the writes)."""
+    check(load().qb_frame_tile_keys(ctypes.byref(frame), ptr(out), out.numel(), stream_handle(stream)))
 
 
 def qb_preprocess(frame: QbFrame, scene: QbScene, camera: QbCamera, mode: int, stream=None):

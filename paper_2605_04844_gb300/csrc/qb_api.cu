@@ -1,4 +1,5 @@
 // qb_api.cu -- the extern "C" entry points of libquadbox (include/quadbox.h).
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -54,6 +55,8 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     L.meta = take(4 * N);
     L.counts = take(4 * N);
     L.offsets = take(4 * N);
+    L.segs = take(64 * N);
+    L.segs_d = take(64 * N);
     L.scan_part = take(8 * scan_partials_count(n));
     L.keys0 = take(8 * cap);
     L.keys1 = take(8 * cap);
@@ -77,6 +80,11 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     }
     L.dsort_scratch = take(db);
     L.ranges = take(8 * (size_t)tiles);
+    const uint64_t n_chunks = (cap + kChunkPairs - 1) / kChunkPairs + 1;
+    L.chunk_start = take(4 * (n_chunks + 1));
+    L.chunk_cnt = take(4 * n_chunks * (size_t)tiles);
+    L.chunk_part = take(4 * (size_t)kChunkSegs * tiles);
+    L.chunk_total = take(4 * (size_t)tiles);
     L.tile_diff = take(4 * (size_t)(tx + 1) * (ty + 1));
     L.tile_single = take(4 * (size_t)tiles);
     L.tfinal = take(4 * (size_t)W * H);
@@ -141,6 +149,15 @@ qb_status check_frame(const qb_frame *f, Layout &L) {
     return QB_OK;
 }
 
+// The sort a frame actually runs: QB_SORT_CHUNKED falls back to the radix
+// tile sort for the naive traversal (whose emit is the nested-loop one) and
+// for images whose per-tile tables exceed the kernels' shared memory.
+int effective_sort(const qb_frame *f, int base_mode) {
+    if (f->sort_mode != QB_SORT_CHUNKED) return f->sort_mode;
+    if (base_mode == QB_BIN_QUADBOX_NAIVE || !chunked_smem_ok(f->tiles_x, f->tiles_y)) return QB_SORT_DEPTH_FIRST;
+    return QB_SORT_CHUNKED;
+}
+
 qb_status check_scene(const qb_frame *f, const qb_scene *s) {
     if (!s) return fail(QB_ERR_INVALID_ARG, "scene is NULL");
     if (s->n != f->n) return fail(QB_ERR_INVALID_ARG, "scene.n (%d) != frame.n (%d)", s->n, f->n);
@@ -164,6 +181,8 @@ qb_status check_camera(const qb_frame *f, const qb_camera *c) {
 
 namespace qb {
 void set_last_error(const char *msg) { g_err = msg; }
+static std::atomic<uint64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace qb
 
 extern "C" {
@@ -171,6 +190,8 @@ extern "C" {
 const char *qb_last_error(void) { return g_err.c_str(); }
 
 const char *qb_version(void) { return "libquadbox 0.1 sm_103a"; }
+
+uint64_t qb_kernel_launches(void) { return qb::g_launches.load(std::memory_order_relaxed); }
 
 size_t qb_frame_workspace_bytes(int32_t n, int32_t width, int32_t height, uint64_t pair_capacity) {
     Layout L;
@@ -235,6 +256,17 @@ qb_status qb_frame_arrays_get(const qb_frame *frame, qb_frame_arrays *out) {
     return QB_OK;
 }
 
+qb_status qb_frame_tile_keys(const qb_frame *frame, uint32_t *d_out, uint64_t n_out, qb_stream_t stream) {
+    Layout L;
+    qb_status st = check_frame(frame, L);
+    if (st != QB_OK) return st;
+    if (frame->stage < 3) return fail(QB_ERR_STATE, "qb_frame_tile_keys before qb_sort");
+    if (!d_out && n_out > 0) return fail(QB_ERR_INVALID_ARG, "output pointer is NULL");
+    QB_CUDA(launch_expand_ranges(at<uint2>(frame, L.ranges), frame->tiles_x * frame->tiles_y, d_out, n_out,
+                                 (cudaStream_t)stream));
+    return QB_OK;
+}
+
 qb_status qb_frame_check(qb_frame *frame, qb_stream_t stream) {
     Layout L;
     qb_status st = check_frame(frame, L);
@@ -260,6 +292,7 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     if (base_mode < QB_BIN_AABB3S || base_mode > QB_BIN_DUALBOX || (mode & ~(0xff | QB_BIN_NO_CLAMP)))
         return fail(QB_ERR_INVALID_ARG, "invalid binning mode %d", mode);
     PreArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.n = scene->n;
     a.means = scene->means;
     a.scales = scene->scales;
@@ -281,9 +314,18 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     a.counts = at<uint32_t>(frame, L.counts);
     a.tile_diff = nullptr;
     a.tile_single = nullptr;
+    a.segs = at<uint4>(frame, L.segs);
     std::memset(a.diff_off, 0, sizeof(a.diff_off));
     std::memset(a.single_off, 0, sizeof(a.single_off));
-    if (frame->sort_mode == QB_SORT_DEPTH_FIRST) {
+    if (frame->sort_mode < QB_SORT_DEPTH_FIRST || frame->sort_mode > QB_SORT_CHUNKED)
+        return fail(QB_ERR_INVALID_ARG, "invalid sort_mode %d", frame->sort_mode);
+    const int eff = effective_sort(frame, base_mode);
+    // the fused emit needs the per-tile counts before it runs: from the
+    // preprocess's difference arrays (also when the grid is too large for the
+    // histogram of the unfused path)
+    const bool fused = eff == QB_SORT_DEPTH_FIRST &&
+                       (frame->emit_fused != 0 || frame->tiles_x * frame->tiles_y > kTileCountMax);
+    if (fused) {
         a.tile_diff = at<int>(frame, L.tile_diff);
         a.tile_single = at<int>(frame, L.tile_single);
         // the two count arrays are adjacent in the workspace: clear them together
@@ -291,7 +333,8 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
                                 (cudaStream_t)stream));
     }
     QB_CUDA(launch_preprocess(a, scene->sh_degree, (cudaStream_t)stream));
-    frame->reserved[0] = frame->sort_mode;  // mode the tile counts were made for
+    // requested sort | effective sort << 8 | fused emit << 16, as the counts were made for
+    frame->reserved[0] = frame->sort_mode | (eff << 8) | ((fused ? 1 : 0) << 16);
     frame->bin_mode = mode;
     frame->sh_degree = scene->sh_degree;
     frame->stage = 1;
@@ -304,16 +347,18 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     qb_status st = check_frame(frame, L);
     if (st != QB_OK) return st;
     if (frame->stage < 1) return fail(QB_ERR_STATE, "qb_bin_emit before qb_preprocess");
-    if (frame->sort_mode != QB_SORT_DEPTH_FIRST && frame->sort_mode != QB_SORT_FULL_KEY)
-        return fail(QB_ERR_INVALID_ARG, "sort_mode must be QB_SORT_DEPTH_FIRST or QB_SORT_FULL_KEY");
-    if (frame->sort_mode != frame->reserved[0])
+    if (frame->sort_mode < QB_SORT_DEPTH_FIRST || frame->sort_mode > QB_SORT_CHUNKED)
+        return fail(QB_ERR_INVALID_ARG, "invalid sort_mode %d", frame->sort_mode);
+    if (frame->sort_mode != (frame->reserved[0] & 0xff))
         return fail(QB_ERR_STATE, "sort_mode changed between qb_preprocess and qb_bin_emit");
+    const int eff = (frame->reserved[0] >> 8) & 0xff;
+    const bool fused = (frame->reserved[0] >> 16) & 1;
     if (frame->sort_digit_bits < 8 || frame->sort_digit_bits > kMaxDigitBits)
         return fail(QB_ERR_INVALID_ARG, "sort_digit_bits must be 8..11");
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t *d_np = at<uint64_t>(frame, L.state);
     uint32_t *err = at<uint32_t>(frame, L.state + 8);
-    const bool depth_first = frame->sort_mode == QB_SORT_DEPTH_FIRST;
+    const bool depth_first = eff != QB_SORT_FULL_KEY;  // Gaussians emitted in depth order
     const uint32_t *perm = nullptr;
     if (depth_first) {
         // emission order = Gaussians sorted by (depth, index)
@@ -329,12 +374,12 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     }
     QB_CUDA(launch_scan(at<uint32_t>(frame, L.counts), perm, frame->n, at<uint32_t>(frame, L.offsets),
                         at<uint64_t>(frame, L.scan_part), d_np, s));
-    if (depth_first) {
+    if (eff == QB_SORT_DEPTH_FIRST && fused) {
         // per-tile counts -> ranges and the tile sort's bucket offsets
         const int tile_bits = frame->key_bits - kDepthBits;
         const int passes = tile_bits > 0 ? (tile_bits + frame->sort_digit_bits - 1) / frame->sort_digit_bits : 0;
         const uint32_t zero_off[1] = {0u};
-        QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), frame_tileset(frame),
+        QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), nullptr, frame_tileset(frame),
                                  zero_off, zero_off,
                                  at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
                                  sort_hist_stride(), frame->sort_digit_bits, passes, frame->pair_capacity, s));
@@ -354,6 +399,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         frame->n_pairs = P;
     }
     EmitArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.n = frame->n;
     a.n_per_cam = frame->n > 0 ? frame->n : 1;
     a.ts = frame_tileset(frame);
@@ -372,10 +418,63 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     a.mode = frame->bin_mode & 0xff;
     a.clamp3s = (frame->bin_mode & QB_BIN_NO_CLAMP) == 0;
     a.err = err;
-    if (depth_first)
-        QB_CUDA(launch_emit<uint32_t>(a, at<uint32_t>(frame, L.keys0), s));
-    else
+    a.segs = at<uint4>(frame, L.segs);
+    if (eff == QB_SORT_CHUNKED) {
+        // per-chunk tile counts, their scan (and the ranges), placement
+        const uint64_t n_max = frame->n_pairs != UINT64_MAX ? frame->n_pairs : frame->pair_capacity;
+        ChunkArgs c;
+        std::memset(&c, 0, sizeof(c));
+        c.tiles_x = frame->tiles_x;
+        c.tiles_y = frame->tiles_y;
+        chunked_bands(c.tiles_x, c.tiles_y, c.band_rows, c.n_bands);
+        c.band_diff_ints = (c.band_rows + 1) * (c.tiles_x + 1);
+        c.band_words = (c.band_rows * c.tiles_x + 3) & ~3;
+        c.chunk_pairs = kChunkPairs;
+        c.n_chunks = (uint32_t)((n_max + kChunkPairs - 1) / kChunkPairs);
+        if (c.n_chunks == 0) c.n_chunks = 1;
+        c.n_segs = kChunkSegs;
+        c.chunks_per_seg = (c.n_chunks + kChunkSegs - 1) / kChunkSegs;
+        c.perm = perm;
+        c.counts = a.counts;
+        c.segs = a.segs;
+        c.segs_d = at<uint4>(frame, L.segs_d);
+        c.n_pairs = d_np;
+        c.capacity = frame->pair_capacity;
+        c.start = at<uint32_t>(frame, L.chunk_start);
+        c.cnt = at<uint32_t>(frame, L.chunk_cnt);
+        c.part = at<uint32_t>(frame, L.chunk_part);
+        c.total = at<uint32_t>(frame, L.chunk_total);
+        a.vals = at<uint32_t>(frame, L.vals0);
+        QB_CUDA(launch_chunked(a, c, at<uint2>(frame, L.ranges), s));
+        frame->reserved[1] = frame->sort_digit_bits;
+        frame->reserved[2] = 0;
+    } else if (depth_first) {
+        // QPass emit in depth order; in the QPass modes it also performs the
+        // tile sort's first digit pass (qb_sort runs the remaining ones)
+        void *scratch = at<void>(frame, L.sort_scratch);
+        const int rb = frame->sort_digit_bits;
+        const int tile_bits = frame->key_bits - kDepthBits;
+        const int passes = tile_bits > 0 ? (tile_bits + rb - 1) / rb : 0;
+        uint32_t *kA = at<uint32_t>(frame, L.keys0), *vA = at<uint32_t>(frame, L.vals0);
+        uint32_t *kB = at<uint32_t>(frame, L.keys1), *vB = at<uint32_t>(frame, L.vals1);
+        if (fused && passes > 0 && a.mode != QB_BIN_QUADBOX_NAIVE) {
+            const bool to_a = pass_writes_a(passes, 0);
+            QB_CUDA(sort_clear(scratch, frame->pair_capacity, rb, 0, 1, s));
+            QB_CUDA(launch_emit_sweep(a, rb, passes > 1, to_a ? kA : kB, to_a ? vA : vB, sort_hist_table(scratch),
+                                      sort_lookback(scratch, frame->pair_capacity, rb, 0), sort_counter(scratch, 0),
+                                      s));
+            frame->reserved[2] = 1;  // first pass left to qb_sort
+        } else {
+            // plain emit into the buffer the first pass reads (or the final one)
+            const bool into_a = passes == 0 || !pass_writes_a(passes, 0);
+            a.vals = into_a ? vA : vB;
+            QB_CUDA(launch_emit<uint32_t>(a, into_a ? kA : kB, s));
+            frame->reserved[2] = 0;
+        }
+        frame->reserved[1] = frame->sort_digit_bits;  // digit width the buffers were chosen for
+    } else {
         QB_CUDA(launch_emit<uint64_t>(a, at<uint64_t>(frame, L.keys0), s));
+    }
     frame->stage = 2;
     return QB_OK;
 }
@@ -394,17 +493,35 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
     int passes = 0;
     const int ntiles = frame->tiles_x * frame->tiles_y;
     uint32_t *err = at<uint32_t>(frame, L.state + 8);
-    if (frame->sort_mode == QB_SORT_DEPTH_FIRST) {
+    const int eff = (frame->reserved[0] >> 8) & 0xff;
+    const bool fused = (frame->reserved[0] >> 16) & 1;
+    if (eff == QB_SORT_CHUNKED) {
+        frame->sorted_in_alt = 0;  // qb_bin_emit placed the values in their sorted positions
+    } else if (eff == QB_SORT_DEPTH_FIRST) {
         // pairs were emitted in depth order: a stable sort on the tile id alone
         // (bucket offsets and ranges came from the per-tile counts in qb_bin_emit)
         if (frame->sort_digit_bits != frame->reserved[1])
             return fail(QB_ERR_STATE, "sort_digit_bits changed between qb_bin_emit and qb_sort");
         const int tile_bits = frame->key_bits - kDepthBits;
-        if (tile_bits > 0)
-            QB_CUDA(sort_pairs(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
-                               at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1), n_max, n_dev, tile_bits,
-                               frame->sort_digit_bits, at<void>(frame, L.sort_scratch), err, s, &passes, true));
-        frame->sorted_in_alt = passes & 1;
+        const int rb = frame->sort_digit_bits;
+        passes = tile_bits > 0 ? (tile_bits + rb - 1) / rb : 0;
+        if (!fused) {
+            // per-tile counts from the emitted tile ids -> ranges and every
+            // pass's bucket offsets
+            const uint32_t *src = at<uint32_t>(frame, passes > 0 && pass_writes_a(passes, 0) ? L.keys1 : L.keys0);
+            uint32_t *counts = at<uint32_t>(frame, L.chunk_total);
+            const uint32_t zero_off[1] = {0u};
+            QB_CUDA(launch_tile_count(src, n_max, n_dev, ntiles, counts, s));
+            QB_CUDA(launch_tile_prep(nullptr, nullptr, counts, frame_tileset(frame), zero_off, zero_off,
+                                     at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
+                                     sort_hist_stride(), rb, passes, frame->pair_capacity, s));
+        }
+        if (passes > 0)
+            QB_CUDA(tile_sort_passes(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
+                                     at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1), frame->pair_capacity,
+                                     n_max, n_dev, passes, frame->reserved[2], rb, at<void>(frame, L.sort_scratch),
+                                     err, s));
+        frame->sorted_in_alt = 0;  // the values end in vals0; the tile of each is given by the ranges
         (void)ntiles;
     } else {
         QB_CUDA(sort_pairs(at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint64_t>(frame, L.keys1),

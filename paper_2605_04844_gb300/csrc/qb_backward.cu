@@ -202,9 +202,9 @@ cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_persistent_kernel, kBwdThreads, 0);
         if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
-        render_bwd_persistent_kernel<<<sms * (per_sm > 0 ? per_sm : 1), kBwdThreads, 0, s>>>(a);
+        note_launch(), render_bwd_persistent_kernel<<<sms * (per_sm > 0 ? per_sm : 1), kBwdThreads, 0, s>>>(a);
     } else {
-        render_bwd_kernel<<<a.ts.total_tiles, kBwdThreads, 0, s>>>(a);
+        note_launch(), render_bwd_kernel<<<a.ts.total_tiles, kBwdThreads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -360,10 +360,10 @@ cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s) 
     if (a.n == 0) return cudaSuccess;
     dim3 grid((a.n + 255) / 256), block(256);
     switch (deg) {
-    case 0: preprocess_bwd_kernel<0><<<grid, block, 0, s>>>(a); break;
-    case 1: preprocess_bwd_kernel<1><<<grid, block, 0, s>>>(a); break;
-    case 2: preprocess_bwd_kernel<2><<<grid, block, 0, s>>>(a); break;
-    default: preprocess_bwd_kernel<3><<<grid, block, 0, s>>>(a); break;
+    case 0: note_launch(), preprocess_bwd_kernel<0><<<grid, block, 0, s>>>(a); break;
+    case 1: note_launch(), preprocess_bwd_kernel<1><<<grid, block, 0, s>>>(a); break;
+    case 2: note_launch(), preprocess_bwd_kernel<2><<<grid, block, 0, s>>>(a); break;
+    default: note_launch(), preprocess_bwd_kernel<3><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

@@ -59,7 +59,7 @@ struct BLayout {
     size_t ranges;                                    // [total tiles]
     size_t tfinal, ncontrib, neval;                   // [total pixels]
     size_t keysA, keysB, valsT;                       // [cap] group scratch
-    size_t offsets, scan_part, dk0, dk1, dv0, dv1;    // [group * n]
+    size_t offsets, segs, scan_part, dk0, dk1, dv0, dv1;  // [group * n]
     size_t dsort, sort, diff, single, gscreen, queue, state;
     size_t total;
 };
@@ -105,6 +105,7 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
     L.keysB = take(4 * cap);
     L.valsT = take(4 * cap);
     L.offsets = take(4 * grecs);
+    L.segs = take(64 * grecs);
     L.scan_part = take(8 * scan_partials_count((int)grecs));
     L.dk0 = take(4 * grecs);
     L.dk1 = take(4 * grecs);
@@ -317,6 +318,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         a.counts = bat<uint32_t>(b, L.counts) + v.rec0;
         a.tile_diff = diff;
         a.tile_single = single;
+        a.segs = bat<uint4>(b, L.segs);
         for (int c = 0; c < v.ncam; ++c) {
             a.diff_off[c] = v.diff_off[c];
             a.single_off[c] = v.single_off[c];
@@ -336,14 +338,15 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         // ---- per-tile counts -> ranges and the tile sort's bucket offsets ----
         const int tpasses = v.tile_bits > 0 ? (v.tile_bits + t.sort_digit_bits - 1) / t.sort_digit_bits : 0;
         uint2 *ranges = bat<uint2>(b, L.ranges) + v.tile0;
-        QB_BCUDA(launch_tile_prep(diff, single, v.ts, v.diff_off, v.single_off, ranges,
+        QB_BCUDA(launch_tile_prep(diff, single, nullptr, v.ts, v.diff_off, v.single_off, ranges,
                                   sort_hist_table(bat<void>(b, L.sort)), sort_hist_stride(), t.sort_digit_bits,
                                   tpasses, b->pair_capacity, s));
-        // ---- QPass emit; the tile sort ends in this group's slot ----
+        // ---- QPass emit fused with the tile sort's first pass; the sorted
+        // values end in this group's slot (buffer A = keysA + slot) ----
         uint32_t *slot = bat<uint32_t>(b, L.slots) + (size_t)gi * b->pair_capacity;
         uint32_t *valsT = bat<uint32_t>(b, L.valsT);
-        uint32_t *vals_in = (tpasses & 1) ? valsT : slot, *vals_alt = (tpasses & 1) ? slot : valsT;
         uint32_t *keysA = bat<uint32_t>(b, L.keysA), *keysB = bat<uint32_t>(b, L.keysB);
+        void *sort_scratch = bat<void>(b, L.sort);
         EmitArgs e;
         std::memset(&e, 0, sizeof(e));
         e.n = nrec;
@@ -356,7 +359,6 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         e.rgbd = a.rgbd;
         e.counts = a.counts;
         e.offsets = bat<uint32_t>(b, L.offsets);
-        e.vals = vals_in;
         e.n_pairs = npairs + gi;
         e.n_pairs_host = UINT64_MAX;
         e.capacity = b->pair_capacity;
@@ -364,11 +366,24 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         e.clamp3s = a.clamp3s;
         e.err = err;
         e.ts = v.ts;
-        QB_BCUDA(launch_emit<uint32_t>(e, keysA, s));
-        int sp = 0;
-        if (v.tile_bits > 0)
-            QB_BCUDA(sort_pairs(keysA, vals_in, keysB, vals_alt, b->pair_capacity, npairs + gi, v.tile_bits,
-                                t.sort_digit_bits, bat<void>(b, L.sort), err, s, &sp, true));
+        e.segs = bat<uint4>(b, L.segs);
+        int first_pass = 0;
+        if (tpasses > 0 && base_mode != QB_BIN_QUADBOX_NAIVE) {
+            const bool to_a = pass_writes_a(tpasses, 0);
+            QB_BCUDA(sort_clear(sort_scratch, b->pair_capacity, t.sort_digit_bits, 0, 1, s));
+            QB_BCUDA(launch_emit_sweep(e, t.sort_digit_bits, tpasses > 1, to_a ? keysA : keysB, to_a ? slot : valsT,
+                                       sort_hist_table(sort_scratch),
+                                       sort_lookback(sort_scratch, b->pair_capacity, t.sort_digit_bits, 0),
+                                       sort_counter(sort_scratch, 0), s));
+            first_pass = 1;
+        } else {
+            const bool into_a = tpasses == 0 || !pass_writes_a(tpasses, 0);
+            e.vals = into_a ? slot : valsT;
+            QB_BCUDA(launch_emit<uint32_t>(e, into_a ? keysA : keysB, s));
+        }
+        if (tpasses > first_pass)
+            QB_BCUDA(tile_sort_passes(keysA, slot, keysB, valsT, b->pair_capacity, b->pair_capacity, npairs + gi,
+                                      tpasses, first_pass, t.sort_digit_bits, sort_scratch, err, s));
         // ---- persistent render over the group's tiles ----
         QB_BCUDA(cudaMemsetAsync(bat<uint32_t>(b, L.queue), 0, 4, s));
         RenderArgs r;

@@ -6,7 +6,7 @@
 // the full-key path, depth order for the depth-first path.  The scan runs in
 // that order, so each Gaussian's pairs are one contiguous run and a warp's 32
 // Gaussians own one contiguous output range.
-#include "qb_kernels.cuh"
+#include "qb_sweep.cuh"
 
 namespace qb {
 
@@ -106,9 +106,9 @@ cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uin
                         uint64_t *n_pairs, cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(n_pairs, 0, sizeof(uint64_t), s);
     int nb = (n + kScanChunk - 1) / kScanChunk;
-    scan_reduce_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials);
-    scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nb, n_pairs);
-    scan_down_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials, offsets);
+    note_launch(), scan_reduce_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials);
+    note_launch(), scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nb, n_pairs);
+    note_launch(), scan_down_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials, offsets);
     return cudaGetLastError();
 }
 
@@ -125,7 +125,7 @@ __global__ void depth_keys_kernel(int n, const float4 *rgbd, const uint32_t *cou
 cudaError_t launch_depth_keys(int n, const float4 *rgbd, const uint32_t *counts, uint32_t *keys, uint32_t *vals,
                               cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    depth_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, rgbd, counts, keys, vals);
+    note_launch(), depth_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, rgbd, counts, keys, vals);
     return cudaGetLastError();
 }
 
@@ -150,37 +150,30 @@ constexpr int kEmitWarps = 8;
 constexpr int kSegPerWarp = 32 * 7;
 constexpr uint32_t kEmitChunk = 2048;  // output positions per warp
 
-// K3 (QPass modes and the single-box modes), balanced over the output: warp w
-// owns the pair positions [w C, (w+1) C).  It finds the first Gaussian whose
-// run reaches into that range (32-ary search over the emission-order
-// offsets), then takes the following Gaussians 32 at a time: each lane
-// decomposes its Gaussian's QPass traversal into segments (runs of scan lines
-// with one merged interval), and the warp writes the range 32 consecutive
-// positions at a time; lane q finds the segment holding its position from a
-// ballot of the segment starts that fall in its group.  Stores are contiguous
-// across the warp, and every warp writes at most C pairs however large the
-// Gaussians are.
-template <typename KeyT>
-__global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, KeyT *__restrict__ keys) {
-    __shared__ int32_t s_start[kEmitWarps][kSegPerWarp];
-    __shared__ uint32_t s_geo[kEmitWarps][kSegPerWarp];
-    __shared__ uint32_t s_len[kEmitWarps][kSegPerWarp];
-    __shared__ float s_inv[kEmitWarps][kSegPerWarp];
-    __shared__ uint32_t s_gid[kEmitWarps][32];
-    __shared__ uint32_t s_dbits[kEmitWarps][32];
-    __shared__ uint32_t s_tbase[kEmitWarps][32];  // first global tile of the owner's camera
-    __shared__ uint32_t s_tx[kEmitWarps][32];     // tiles per row of the owner's camera
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint64_t P = *a.n_pairs;
-    const uint64_t warp_id = (uint64_t)blockIdx.x * kEmitWarps + wid;
-    if (P > a.capacity) {
-        if (warp_id == 0 && lane == 0) atomicOr(a.err, kErrCapacity);
-        return;
-    }
-    const uint64_t C = warp_id * kEmitChunk;
-    if (C >= P || a.n == 0) return;
-    const int32_t L = (int32_t)min((uint64_t)kEmitChunk, P - C);
+// One warp's table of QPass segments for a batch of 32 Gaussians.
+struct SegTable {
+    int32_t start[kSegPerWarp];  // chunk position of the segment's first pair
+    uint32_t geo[kSegPerWarp];   // first line | first cell << 16
+    uint32_t len[kSegPerWarp];   // cells per line | owner lane << 16 | column flag << 24
+    float inv[kSegPerWarp];      // 1 / cells per line
+    uint32_t gid[32], dbits[32];
+    uint32_t tbase[32];  // first global tile of the owner's camera
+    uint32_t tx[32];     // tiles per row of the owner's camera
+};
 
+// K3 (QPass modes and the single-box modes) for the pair positions
+// [C, C + L) of the emission order, run by one warp.  It finds the first
+// Gaussian whose run reaches into that range (32-ary search over the
+// emission-order offsets), then takes the following Gaussians 32 at a time:
+// each lane decomposes its Gaussian's QPass traversal into segments (runs of
+// scan lines with one merged interval), and the warp produces the range 32
+// consecutive positions at a time; lane q finds the segment holding its
+// position from a ballot of the segment starts that fall in its group.
+// sink(valid, p, tile, gid, depth bits) is called by all 32 lanes together
+// once per group of 32 positions; valid lanes carry position C + p.
+template <typename KeyOut, class Sink>
+__device__ __forceinline__ void emit_range(const EmitArgs &a, uint64_t C, int32_t L, SegTable &S, Sink &&sink) {
+    const int lane = threadIdx.x & 31;
     // last emission position j with offsets[j] <= C (offsets are non-decreasing)
     int64_t lo = 0, hi = a.n - 1;  // invariant: offsets[lo] <= C, answer in [lo, hi]
     while (hi > lo) {
@@ -199,7 +192,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
     int64_t j0 = lo;
 
     const uint32_t le_mask = lanemask_le();
-    int32_t done_to = 0;  // chunk positions [0, done_to) written
+    int32_t done_to = 0;  // chunk positions [0, done_to) produced
     while (done_to < L && j0 < a.n) {
         const int64_t j = j0 + lane;
         uint32_t gid = 0, cnt = 0;
@@ -211,40 +204,58 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
         }
         const bool relevant = cnt > 0u && rel < L && rel + (int64_t)cnt > 0;
         QSeg seg[7];
-        int ns = 0;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) seg[q] = QSeg{0, 0, 0, 0};
         bool columns = false;
         uint32_t dbits = 0, tbase = 0, tx_n = 1;
         if (relevant) {
+            // the preprocess's segment record (slots beyond its count are zero)
             const CamTile &cam = a.ts.cam[gid / (uint32_t)a.n_per_cam];
             tbase = cam.tile_base;
             tx_n = (uint32_t)cam.tiles_x;
-            const float2 xy = a.xy[gid];
-            const int meta = a.meta[gid];
-            dbits = __float_as_uint(a.rgbd[gid].w) & 0x7fffffffu;
-            Rect r[4];
-            box_rects(xy.x, xy.y, a.box[gid], a.r3[gid], (meta & kMetaOrient) != 0, a.mode, a.clamp3s, cam.W,
-                      cam.H, r);
-            QPass qp;
-            if (qpass_setup(r, qp)) {
-                ns = qpass_segments(qp, seg);
-                columns = qp.columns;
+            if (sizeof(KeyOut) == 8) dbits = __float_as_uint(a.rgbd[gid].w) & 0x7fffffffu;
+            const uint4 *src = a.segs + 4 * (size_t)gid;
+            uint32_t w[16];
+            const uint4 c0 = src[0];
+            w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
+            const int n_in = (int)(c0.x & 7u);
+            columns = (c0.x >> 3) & 1u;
+            const int nc = seg_chunks(n_in);
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {
+                const uint4 v = c < nc ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+                w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                if (q >= n_in) continue;
+                seg[q].s0 = (int)(w[1 + 2 * q] & 0xffffu);
+                seg[q].lo = (int)(w[1 + 2 * q] >> 16);
+                seg[q].nl = (int)(w[2 + 2 * q] & 0xffffu);
+                seg[q].len = (int)(w[2 + 2 * q] >> 16);
             }
         }
+        int ns = 0;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) ns += seg_empty(seg[q]) ? 0 : 1;
         __syncwarp();
-        s_gid[wid][lane] = gid;
-        s_dbits[wid][lane] = dbits;
-        s_tbase[wid][lane] = tbase;
-        s_tx[wid][lane] = tx_n;
+        S.gid[lane] = gid;
+        S.dbits[lane] = dbits;
+        S.tbase[lane] = tbase;
+        S.tx[lane] = tx_n;
         const int sincl = warp_incl_scan(ns);
-        const int sbase = sincl - ns;
         const int nseg = __shfl_sync(0xffffffffu, sincl, 31);
         int32_t r0 = (int32_t)(rel > -((int64_t)1 << 30) ? rel : -((int64_t)1 << 30));
-        for (int q = 0; q < ns; ++q) {
-            s_start[wid][sbase + q] = r0;
-            s_geo[wid][sbase + q] = (uint32_t)seg[q].s0 | ((uint32_t)seg[q].lo << 16);
-            s_len[wid][sbase + q] = (uint32_t)seg[q].len | ((uint32_t)lane << 16) | ((uint32_t)columns << 24);
-            s_inv[wid][sbase + q] = 1.0f / (float)seg[q].len;
+        int k = sincl - ns;  // this lane's first table entry
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            if (seg_empty(seg[q])) continue;
+            S.start[k] = r0;
+            S.geo[k] = (uint32_t)seg[q].s0 | ((uint32_t)seg[q].lo << 16);
+            S.len[k] = (uint32_t)seg[q].len | ((uint32_t)lane << 16) | ((uint32_t)columns << 24);
+            S.inv[k] = 1.0f / (float)seg[q].len;
             r0 += seg[q].nl * seg[q].len;
+            ++k;
         }
         // end of this batch's pairs within the chunk
         const int64_t last_end = __shfl_sync(0xffffffffu, rel + (int64_t)cnt, 31);
@@ -253,26 +264,28 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
         // cur: last segment starting at or before done_to
         int cur = -1;
         for (int b = 0; b < nseg; b += 32) {
-            const bool le = b + lane < nseg && s_start[wid][b + lane] <= done_to;
+            const bool le = b + lane < nseg && S.start[b + lane] <= done_to;
             cur += __popc(__ballot_sync(0xffffffffu, le));
         }
         for (int32_t c0 = done_to; c0 < batch_end; c0 += 32) {
             const int cand = cur + 1 + lane;
             uint32_t bit = 0u;
             if (cand < nseg) {
-                const int32_t st = s_start[wid][cand];
+                const int32_t st = S.start[cand];
                 if (st < c0 + 32) bit = 1u << (st - c0);
             }
             const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
             const int32_t p = c0 + lane;
-            if (p < batch_end) {
+            const bool valid = p < batch_end;
+            uint32_t tile = 0u, gid_out = 0u, dbits_out = 0u;
+            if (valid) {
                 const int idx = cur + __popc(M & le_mask);
-                const int32_t st = s_start[wid][idx];
-                const uint32_t geo = s_geo[wid][idx], ln = s_len[wid][idx];
+                const int32_t st = S.start[idx];
+                const uint32_t geo = S.geo[idx], ln = S.len[idx];
                 const uint32_t k = (uint32_t)(p - st), len = ln & 0xffffu;
                 // k / len through the reciprocal (k < 2^24, so the estimate is
                 // off by at most one) and one exact correction
-                int32_t q = (int32_t)((float)k * s_inv[wid][idx]);
+                int32_t q = (int32_t)((float)k * S.inv[idx]);
                 int32_t r = (int32_t)k - q * (int32_t)len;
                 if (r < 0) { --q; r += (int32_t)len; }
                 if (r >= (int32_t)len) { ++q; r -= (int32_t)len; }
@@ -280,15 +293,136 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
                 const uint32_t u = (geo >> 16) + (uint32_t)r;
                 const bool cols = (ln >> 24) & 1u;
                 const uint32_t owner = (ln >> 16) & 0xffu;
-                const uint32_t tile = s_tbase[wid][owner] + (cols ? u : line) * s_tx[wid][owner] + (cols ? line : u);
-                keys[C + p] = make_key<KeyT>(tile, s_dbits[wid][owner]);
-                a.vals[C + p] = s_gid[wid][owner];
+                tile = S.tbase[owner] + (cols ? u : line) * S.tx[owner] + (cols ? line : u);
+                gid_out = S.gid[owner];
+                dbits_out = S.dbits[owner];
             }
+            sink(valid, p, tile, gid_out, dbits_out);  // all lanes, converged
             cur += __popc(M);
         }
         done_to = max(done_to, batch_end);
         j0 += 32;
     }
+}
+
+// K3 balanced over the output: warp w owns the pair positions
+// [w C, (w+1) C), so stores are contiguous across the warp and every warp
+// writes at most C pairs however large the Gaussians are.
+template <typename KeyT>
+__global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, KeyT *__restrict__ keys) {
+    __shared__ SegTable s_seg[kEmitWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t P = *a.n_pairs;
+    const uint64_t warp_id = (uint64_t)blockIdx.x * kEmitWarps + wid;
+    if (P > a.capacity) {
+        if (warp_id == 0 && lane == 0) atomicOr(a.err, kErrCapacity);
+        return;
+    }
+    const uint64_t C = warp_id * kEmitChunk;
+    if (C >= P || a.n == 0) return;
+    const int32_t L = (int32_t)min((uint64_t)kEmitChunk, P - C);
+    uint32_t *vals = a.vals;
+    emit_range<KeyT>(a, C, L, s_seg[wid], [&](bool valid, int32_t p, uint32_t tile, uint32_t gid, uint32_t dbits) {
+        if (valid) {
+            keys[C + p] = make_key<KeyT>(tile, dbits);
+            vals[C + p] = gid;
+        }
+    });
+}
+
+// K3 fused with the first (lowest-digit) pass of the depth-first tile sort:
+// a block of 16 warps produces the 4096 pairs of one sort tile into shared
+// memory (warp w the positions [256 w, 256 w + 256)), then runs the pass
+// body on them, so the pairs reach HBM once, already bucketed by their low
+// tile digit.  The bucket offsets of the pass come from the per-tile counts.
+constexpr size_t kEmitSweepStage = (size_t)2 * kSortTile * 4;
+
+template <int RB>
+constexpr size_t emit_sweep_smem() {
+    return kEmitSweepStage + kSortWarps * sizeof(SegTable) > sweep_smem<RB, uint32_t>()
+               ? kEmitSweepStage + kSortWarps * sizeof(SegTable)
+               : sweep_smem<RB, uint32_t>();
+}
+
+template <int RB, bool WRITE_KEYS>
+__global__ void __launch_bounds__(kSortBlock) emit_sweep_kernel(EmitArgs a, uint32_t *__restrict__ kout,
+                                                                uint32_t *__restrict__ vout,
+                                                                const uint32_t *__restrict__ bin_off,
+                                                                uint32_t *lookback, uint32_t *counter) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *s_k = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *s_v = s_k + kSortTile;
+    SegTable *s_seg = reinterpret_cast<SegTable *>(smem + kEmitSweepStage);
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t P = *a.n_pairs;
+    if (P > a.capacity) {  // block-uniform
+        if (tile == 0 && tid == 0) atomicOr(a.err, kErrCapacity);
+        return;
+    }
+    const uint64_t tbase = (uint64_t)tile * kSortTile;
+    if (tbase >= P) return;  // block-uniform
+    constexpr int kWarpSpan = 32 * kSortItems;
+    const uint64_t C = tbase + (uint64_t)wid * kWarpSpan;
+    const int32_t L = C < P ? (int32_t)min((uint64_t)kWarpSpan, P - C) : 0;
+    uint32_t *wk = s_k + wid * kWarpSpan, *wv = s_v + wid * kWarpSpan;
+    if (L > 0)
+        emit_range<uint32_t>(a, C, L, s_seg[wid], [&](bool valid, int32_t p, uint32_t tile_id, uint32_t gid, uint32_t) {
+            if (valid) {
+                wk[p] = tile_id;
+                wv[p] = gid;
+            }
+        });
+    __syncthreads();
+    uint32_t key[kSortItems], val[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const int q = 32 * k + lane;
+        const bool valid = q < L;
+        key[k] = valid ? wk[q] : ~0u;
+        val[k] = valid ? wv[q] : 0u;
+    }
+    __syncthreads();  // the pass body reuses the staging memory
+    sweep_tile<RB, uint32_t, WRITE_KEYS>(key, val, P, tbase, tile, bin_off, lookback, 0, a.err, kout, vout, smem);
+}
+
+template <int RB, bool WRITE_KEYS>
+static cudaError_t launch_emit_sweep_b(const EmitArgs &a, uint32_t *kout, uint32_t *vout, const uint32_t *bin_off,
+                                       uint32_t *lookback, uint32_t *counter, cudaStream_t s) {
+    static bool attrs = false;
+    constexpr size_t smem = emit_sweep_smem<RB>();
+    if (!attrs) {
+        cudaError_t e = cudaFuncSetAttribute(emit_sweep_kernel<RB, WRITE_KEYS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attrs = true;
+    }
+    const uint64_t pairs = a.n_pairs_host != UINT64_MAX ? a.n_pairs_host : a.capacity;
+    uint64_t blocks = (pairs + kSortTile - 1) / kSortTile;
+    if (blocks == 0) blocks = 1;  // one block still flags an overflow
+    note_launch(), emit_sweep_kernel<RB, WRITE_KEYS><<<(unsigned)blocks, kSortBlock, smem, s>>>(a, kout, vout, bin_off, lookback,
+                                                                               counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_sweep(const EmitArgs &a, int digit_bits, bool write_keys, uint32_t *kout, uint32_t *vout,
+                              const uint32_t *bin_off, uint32_t *lookback, uint32_t *counter, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+#define QB_SWEEP_CASE(RB)                                                                                        \
+    case RB:                                                                                                     \
+        return write_keys ? launch_emit_sweep_b<RB, true>(a, kout, vout, bin_off, lookback, counter, s)          \
+                          : launch_emit_sweep_b<RB, false>(a, kout, vout, bin_off, lookback, counter, s);
+    switch (digit_bits) {
+        QB_SWEEP_CASE(8)
+        QB_SWEEP_CASE(9)
+        QB_SWEEP_CASE(10)
+        QB_SWEEP_CASE(11)
+    default: return cudaErrorInvalidValue;
+    }
+#undef QB_SWEEP_CASE
 }
 
 // K3 for QuadBox-dagger (QB_BIN_QUADBOX_NAIVE, the paper's ablation without
@@ -332,13 +466,13 @@ template <typename KeyT>
 cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (a.mode == QB_BIN_QUADBOX_NAIVE) {
-        emit_naive_kernel<KeyT><<<(a.n + 255) / 256, 256, 0, s>>>(a, keys);
+        note_launch(), emit_naive_kernel<KeyT><<<(a.n + 255) / 256, 256, 0, s>>>(a, keys);
     } else {
         const uint64_t pairs = a.n_pairs_host != UINT64_MAX ? a.n_pairs_host : a.capacity;
         const uint64_t warps = (pairs + kEmitChunk - 1) / kEmitChunk;
         const uint64_t blocks = (warps + kEmitWarps - 1) / kEmitWarps;
-        if (blocks > 0) emit_warp_kernel<KeyT><<<(unsigned)blocks, kEmitWarps * 32, 0, s>>>(a, keys);
-        else if (a.n > 0) emit_warp_kernel<KeyT><<<1, kEmitWarps * 32, 0, s>>>(a, keys);  // flags overflow
+        if (blocks > 0) note_launch(), emit_warp_kernel<KeyT><<<(unsigned)blocks, kEmitWarps * 32, 0, s>>>(a, keys);
+        else if (a.n > 0) note_launch(), emit_warp_kernel<KeyT><<<1, kEmitWarps * 32, 0, s>>>(a, keys);  // flags overflow
     }
     return cudaGetLastError();
 }
@@ -372,7 +506,470 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
     if (e != cudaSuccess || n_max == 0) return e;
     uint64_t blocks = (n_max + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    ranges_kernel<KeyT><<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges, (uint32_t)ntiles);
+    note_launch(), ranges_kernel<KeyT><<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges, (uint32_t)ntiles);
+    return cudaGetLastError();
+}
+
+// ---- chunked counting placement (QB_SORT_CHUNKED) ---------------------------
+// The depth-ordered pair stream is cut into chunks of Gaussians whose first
+// pairs fall in [c K, (c+1) K).  Per chunk and tile the pairs are counted
+// from the Gaussians' QPass segments with a 2D difference array in shared
+// memory; an exclusive scan of the counts over the chunks (per tile, plus the
+// tile ranges) gives every (chunk, tile) its first output position; and one
+// warp per chunk walks its pairs in order and places each at its tile's
+// running position.  Pairs of one tile thus keep the emission (depth, index)
+// order, which is exactly the stable sort by tile of the depth-ordered pairs.
+
+// start[c] = first emission position j with offsets[j] >= min(c K, P): the
+// Gaussians without tiles (all at the end of the depth order, offset P) fall
+// in no chunk.
+__global__ void chunk_start_kernel(const uint32_t *__restrict__ offsets, int n, uint32_t n_chunks, uint32_t K,
+                                   const uint64_t *n_pairs, uint32_t *start) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n_chunks) return;
+    const uint64_t P = *n_pairs;
+    const uint64_t target = (uint64_t)c * K < P ? (uint64_t)c * K : P;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((uint64_t)offsets[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    start[c] = (uint32_t)lo;
+}
+
+// A chunk is processed in bands of tile rows, one warp per (chunk, band):
+// a band's tables fit a few KB of shared memory, so many warps run per SM.
+
+// The segments of one record (src, whose first uint4 c0 the caller has
+// loaded) clipped to tile rows [y0, y1), in fixed slots (empty ones zero; ns
+// counts the others); returns their pair count (0 when the Gaussian misses
+// the band).
+
+// Records in emission order, for the chunk tasks' contiguous reads.
+__global__ void chunk_gather_kernel(ChunkArgs a, int n) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= (uint32_t)n || j >= a.start[a.n_chunks]) return;  // Gaussians without tiles are never read
+    const uint4 *src = a.segs + 4 * (size_t)a.perm[j];
+    uint4 *dst = a.segs_d + 4 * (size_t)j;
+    const uint4 c0 = src[0];
+    dst[0] = c0;
+    const int nc = seg_chunks((int)(c0.x & 7u));
+    for (int q = 1; q < nc; ++q) dst[q] = src[q];
+}
+
+__device__ __forceinline__ uint32_t band_segments(const uint4 *__restrict__ src, uint4 c0, int y0, int y1,
+                                                  QSeg seg[7], int &ns, bool &columns) {
+    ns = 0;
+    columns = false;
+    const int ylo = (int)((c0.x >> 4) & 0x3fffu), yhi = (int)((c0.x >> 18) & 0x3fffu);
+    if (yhi < y0 || ylo >= y1) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) seg[q] = QSeg{0, 0, 0, 0};
+        return 0u;
+    }
+    const int n_in = (int)(c0.x & 7u);
+    columns = (c0.x >> 3) & 1u;
+    uint32_t w[16];
+    w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
+    const int nc = seg_chunks(n_in);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+        const uint4 v = q < nc ? src[q] : make_uint4(0u, 0u, 0u, 0u);
+        w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+    }
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        seg[q] = QSeg{0, 0, 0, 0};
+        if (q >= n_in) continue;
+        int s0 = (int)(w[1 + 2 * q] & 0xffffu), lo = (int)(w[1 + 2 * q] >> 16);
+        int nl = (int)(w[2 + 2 * q] & 0xffffu), len = (int)(w[2 + 2 * q] >> 16);
+        if (columns) {  // lines are columns: clip the interval (rows)
+            const int a = max(lo, y0), b = min(lo + len, y1);
+            lo = a;
+            len = b - a;
+        } else {  // lines are rows: clip the lines
+            const int a = max(s0, y0), b = min(s0 + nl, y1);
+            s0 = a;
+            nl = b - a;
+        }
+        if (nl <= 0 || len <= 0) continue;
+        seg[q] = QSeg{s0, lo, nl, len};
+        ++ns;
+        cnt += (uint32_t)(nl * len);
+    }
+    return cnt;
+}
+
+// Per (chunk, band): the band's tile counts cnt[c][t] from a 2D difference
+// array of the clipped segments.  Four warps (bands) per block.
+constexpr int kBandWarps = 4;
+
+__global__ void __launch_bounds__(kBandWarps * 32) chunk_count_kernel(ChunkArgs a) {
+    extern __shared__ int s_diff[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int band = blockIdx.x * kBandWarps + wid;
+    const uint32_t c = blockIdx.y;
+    if (band >= a.n_bands) return;  // warp-uniform; only warp-level syncs below
+    const int tx = a.tiles_x, T = tx * a.tiles_y, stride = tx + 1;
+    const int y0 = band * a.band_rows, y1 = min(a.tiles_y, y0 + a.band_rows), rows = y1 - y0;
+    int *D = s_diff + wid * a.band_diff_ints;
+    for (int k = lane; k < (rows + 1) * stride; k += 32) D[k] = 0;
+    __syncwarp();
+    if (*a.n_pairs > a.capacity) return;  // flagged by the emit
+    const uint32_t j0 = a.start[c], j1 = a.start[c + 1];
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    uint4 h = j0 + lane < j1 ? a.segs_d[4 * (size_t)(j0 + lane)] : zero4;
+    for (uint32_t j = j0 + lane; j < j1; j += 32) {
+        const uint4 hc = h;
+        h = j + 32 < j1 ? a.segs_d[4 * (size_t)(j + 32)] : zero4;  // next record's header, early
+        QSeg seg[7];
+        int ns;
+        bool columns;
+        if (band_segments(a.segs_d + 4 * (size_t)j, hc, y0, y1, seg, ns, columns) == 0u) continue;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            if (seg_empty(seg[q])) continue;
+            const int l0 = seg[q].s0, l1 = seg[q].s0 + seg[q].nl - 1;
+            const int u0 = seg[q].lo, u1 = seg[q].lo + seg[q].len - 1;
+            const int x0 = columns ? l0 : u0, x1 = columns ? l1 : u1;
+            const int ya = (columns ? u0 : l0) - y0, yb = (columns ? u1 : l1) - y0;
+            atomicAdd(D + ya * stride + x0, 1);
+            atomicAdd(D + ya * stride + x1 + 1, -1);
+            atomicAdd(D + (yb + 1) * stride + x0, -1);
+            atomicAdd(D + (yb + 1) * stride + x1 + 1, 1);
+        }
+    }
+    __syncwarp();
+    for (int r = 0; r < rows; ++r) {  // prefix along x
+        int carry = 0;
+        for (int x0 = 0; x0 < tx; x0 += 32) {
+            const int x = x0 + lane;
+            const int v = x < tx ? D[r * stride + x] : 0;
+            const int incl = warp_incl_scan(v) + carry;
+            if (x < tx) D[r * stride + x] = incl;
+            carry = __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncwarp();
+    uint32_t *row = a.cnt + (size_t)c * T + (size_t)y0 * tx;
+    for (int x = lane; x < tx; x += 32) {  // prefix along y, and out
+        int run = 0;
+        for (int r = 0; r < rows; ++r) {
+            run += D[r * stride + x];
+            row[r * tx + x] = (uint32_t)run;
+        }
+    }
+}
+
+// part[s][t] = sum of cnt[c][t] over the chunks of segment s.
+__global__ void chunk_part_kernel(ChunkArgs a) {
+    const int T = a.tiles_x * a.tiles_y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint32_t s = blockIdx.y;
+    const uint32_t c0 = s * a.chunks_per_seg, c1 = min(c0 + a.chunks_per_seg, a.n_chunks);
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (uint32_t c = c0; c < c1; ++c) sum += a.cnt[(size_t)c * T + t];
+    a.part[(size_t)s * T + t] = sum;
+}
+
+// Per tile: exclusive scan of part over the chunk segments, and the tile's
+// total.
+__global__ void chunk_tile_scan_kernel(ChunkArgs a) {
+    const int T = a.tiles_x * a.tiles_y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    uint32_t v[kChunkSegs];
+#pragma unroll
+    for (uint32_t q = 0; q < kChunkSegs; ++q) v[q] = q < a.n_segs ? a.part[(size_t)q * T + t] : 0u;
+    uint32_t run = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kChunkSegs; ++q) {
+        if (q < a.n_segs) a.part[(size_t)q * T + t] = run;
+        run += v[q];
+    }
+    a.total[t] = run;
+}
+
+// The ranges: exclusive scan of the tile totals over the tiles (one block);
+// total[t] becomes the tile's first position.
+__global__ void __launch_bounds__(1024) chunk_ranges_kernel(ChunkArgs a, uint2 *ranges) {
+    const int T = a.tiles_x * a.tiles_y;
+    const int per = (T + blockDim.x - 1) / blockDim.x;
+    const int t0 = threadIdx.x * per, t1 = min(T, t0 + per);
+    uint64_t local64 = 0;
+    for (int t = t0; t < t1; ++t) local64 += a.total[t];
+    uint64_t total64;
+    block_incl_scan<uint64_t>(local64, &total64);
+    // more pairs than the buffers hold: the count kernel wrote no table, the
+    // emit writes nothing, and every tile is left empty
+    const bool over = *a.n_pairs > a.capacity || total64 > a.capacity;
+    uint32_t local = over ? 0u : (uint32_t)local64;
+    uint32_t tot;
+    uint32_t run = block_incl_scan<uint32_t>(local, &tot) - local;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t v = over ? 0u : a.total[t];
+        ranges[t] = v ? make_uint2(run, run + v) : make_uint2(0u, 0u);
+        a.total[t] = run;
+        run += v;
+    }
+}
+
+// cnt[c][t] <- first output position of chunk c's pairs in tile t.
+__global__ void chunk_base_kernel(ChunkArgs a) {
+    const int T = a.tiles_x * a.tiles_y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint32_t s = blockIdx.y;
+    const uint32_t c0 = s * a.chunks_per_seg, c1 = min(c0 + a.chunks_per_seg, a.n_chunks);
+    uint32_t run = a.total[t] + a.part[(size_t)s * T + t];
+    for (uint32_t cb = c0; cb < c1; cb += 8) {
+        uint32_t v[8];  // loads first, then the stores (they cannot alias)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = cb + k < c1 ? a.cnt[(size_t)(cb + k) * T + t] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (cb + k < c1) a.cnt[(size_t)(cb + k) * T + t] = run;
+            run += v[k];
+        }
+    }
+}
+
+// Per (chunk, band): the chunk's Gaussians in emission order, their pairs in
+// the band generated 32 at a time (QPass segments, as in emit_range), and each
+// pair written at its tile's running position.  Lanes of a group of 32 that
+// share a tile are found with one ballot per tile-id bit that varies in the
+// group, and ranked in lane (emission) order.
+__global__ void __launch_bounds__(kBandWarps * 32) chunk_emit_kernel(EmitArgs e, ChunkArgs a) {
+    extern __shared__ __align__(16) uint8_t s_band[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int band = blockIdx.x * kBandWarps + wid;
+    const uint32_t c = blockIdx.y;
+    const uint64_t P = *e.n_pairs;
+    if (P > e.capacity) {
+        if (c == 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(e.err, kErrCapacity);
+        return;
+    }
+    if (band >= a.n_bands) return;  // warp-uniform
+    const int tx = a.tiles_x, T = tx * a.tiles_y;
+    const int y0 = band * a.band_rows, y1 = min(a.tiles_y, y0 + a.band_rows);
+    const uint32_t t0 = (uint32_t)y0 * tx, nb = (uint32_t)(y1 - y0) * tx;
+    uint8_t *mine = s_band + (size_t)wid * ((size_t)a.band_words * 4 + sizeof(SegTable));
+    uint32_t *cursor = reinterpret_cast<uint32_t *>(mine);
+    SegTable &S = *reinterpret_cast<SegTable *>(mine + (size_t)a.band_words * 4);
+    const uint32_t j0 = a.start[c], j1 = a.start[c + 1];
+    if (j0 >= j1) return;
+    const uint32_t *row = a.cnt + (size_t)c * T + t0;
+    for (uint32_t k = lane; k < nb; k += 32) cursor[k] = row[k];
+    __syncwarp();
+    uint32_t *vals = e.vals;
+    const uint64_t cap = e.capacity;
+    const uint32_t lt = lanemask_lt(), le_mask = lanemask_le();
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    uint4 h = j0 + lane < j1 ? a.segs_d[4 * (size_t)(j0 + lane)] : zero4;
+    uint32_t gn = j0 + lane < j1 ? a.perm[j0 + lane] : 0u;
+    for (uint32_t jb = j0; jb < j1; jb += 32) {
+        const uint32_t j = jb + lane;
+        const uint4 hc = h;
+        const uint32_t g = gn;
+        if (j + 32 < j1) {  // the next batch's header and index, early
+            h = a.segs_d[4 * (size_t)(j + 32)];
+            gn = a.perm[j + 32];
+        }
+        QSeg seg[7];
+        int ns = 0;
+        bool columns = false;
+        uint32_t cnt = 0u;
+        if (j < j1) cnt = band_segments(a.segs_d + 4 * (size_t)j, hc, y0, y1, seg, ns, columns);
+        const uint32_t incl = warp_incl_scan(cnt);
+        const uint32_t btotal = __shfl_sync(0xffffffffu, incl, 31);
+        if (btotal == 0u) continue;  // warp-uniform
+        const int sincl = warp_incl_scan(ns);
+        const int nseg = __shfl_sync(0xffffffffu, sincl, 31);
+        __syncwarp();
+        S.gid[lane] = g;
+        int32_t r0 = (int32_t)(incl - cnt);
+        int k = sincl - ns;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            if (seg_empty(seg[q])) continue;
+            S.start[k] = r0;
+            S.geo[k] = (uint32_t)seg[q].s0 | ((uint32_t)seg[q].lo << 16);
+            S.len[k] = (uint32_t)seg[q].len | ((uint32_t)lane << 16) | ((uint32_t)columns << 24);
+            S.inv[k] = 1.0f / (float)seg[q].len;
+            r0 += seg[q].nl * seg[q].len;
+            ++k;
+        }
+        __syncwarp();
+        int cur = -1;  // last segment starting at or before the group's first position
+        for (int32_t c0 = 0; c0 < (int32_t)btotal; c0 += 32) {
+            const int cand = cur + 1 + lane;
+            uint32_t bit = 0u;
+            if (cand < nseg) {
+                const int32_t st = S.start[cand];
+                if (st < c0 + 32) bit = 1u << (st - c0);
+            }
+            const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
+            const int32_t p = c0 + lane;
+            const bool valid = p < (int32_t)btotal;
+            uint32_t key = 4096u + (uint32_t)lane, gid = 0u;  // invalid lanes: keys no band tile has
+            if (valid) {
+                const int idx = cur + __popc(M & le_mask);
+                const int32_t st = S.start[idx];
+                const uint32_t geo = S.geo[idx], ln = S.len[idx];
+                const uint32_t k = (uint32_t)(p - st), len = ln & 0xffffu;
+                int32_t q = (int32_t)((float)k * S.inv[idx]);
+                int32_t r = (int32_t)k - q * (int32_t)len;
+                if (r < 0) { --q; r += (int32_t)len; }
+                if (r >= (int32_t)len) { ++q; r -= (int32_t)len; }
+                const uint32_t line = (geo & 0xffffu) + (uint32_t)q;
+                const uint32_t u = (geo >> 16) + (uint32_t)r;
+                const bool cols = (ln >> 24) & 1u;
+                const uint32_t tile = (cols ? u : line) * (uint32_t)tx + (cols ? line : u);
+                key = tile - t0;
+                gid = S.gid[(ln >> 16) & 0xffu];
+            }
+            cur += __popc(M);
+            // lanes with the same key: one ballot per varying key bit
+            const uint32_t vary = __reduce_or_sync(0xffffffffu, key) ^ __reduce_and_sync(0xffffffffu, key);
+            uint32_t peers = 0xffffffffu, vb = vary;
+            while (vb) {
+                const int b = __ffs(vb) - 1;
+                vb &= vb - 1u;
+                const bool set = (key >> b) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, set);
+                peers &= set ? bb : ~bb;
+            }
+            const uint32_t rank = __popc(peers & lt);
+            uint32_t base = 0u;
+            if (valid && rank == 0u) {
+                base = cursor[key];
+                cursor[key] = base + (uint32_t)__popc(peers);
+            }
+            base = __shfl_sync(0xffffffffu, base, __ffs(peers) - 1);
+            const uint64_t pos = (uint64_t)base + rank;
+            if (valid && pos < cap) vals[pos] = gid;
+            __syncwarp();
+        }
+    }
+}
+
+cudaError_t launch_chunked(const EmitArgs &e, const ChunkArgs &a, uint2 *ranges, cudaStream_t s) {
+    const int T = a.tiles_x * a.tiles_y;
+    if (e.n == 0 || T == 0) return cudaSuccess;
+    note_launch(), chunk_start_kernel<<<(a.n_chunks + 1 + 255) / 256, 256, 0, s>>>(e.offsets, e.n, a.n_chunks,
+                                                                                a.chunk_pairs, e.n_pairs, a.start);
+    const size_t smem_count = (size_t)kBandWarps * a.band_diff_ints * 4;
+    const size_t smem_emit = (size_t)kBandWarps * ((size_t)a.band_words * 4 + sizeof(SegTable));
+    static size_t set_count = 0, set_emit = 0;
+    cudaError_t err;
+    if (smem_count > set_count) {
+        if ((err = cudaFuncSetAttribute(chunk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_count)) != cudaSuccess)
+            return err;
+        set_count = smem_count;
+    }
+    if (smem_emit > set_emit) {
+        if ((err = cudaFuncSetAttribute(chunk_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_emit)) != cudaSuccess)
+            return err;
+        set_emit = smem_emit;
+    }
+    note_launch(), chunk_gather_kernel<<<(e.n + 255) / 256, 256, 0, s>>>(a, e.n);
+    const dim3 bg((a.n_bands + kBandWarps - 1) / kBandWarps, a.n_chunks);
+    note_launch(), chunk_count_kernel<<<bg, kBandWarps * 32, smem_count, s>>>(a);
+    const dim3 tg((T + 255) / 256, a.n_segs);
+    note_launch(), chunk_part_kernel<<<tg, 256, 0, s>>>(a);
+    note_launch(), chunk_tile_scan_kernel<<<(T + 255) / 256, 256, 0, s>>>(a);
+    note_launch(), chunk_ranges_kernel<<<1, 1024, 0, s>>>(a, ranges);
+    note_launch(), chunk_base_kernel<<<tg, 256, 0, s>>>(a);
+    note_launch(), chunk_emit_kernel<<<bg, kBandWarps * 32, smem_emit, s>>>(e, a);
+    return cudaGetLastError();
+}
+
+// Band geometry of the chunked placement for a tiles_x x tiles_y grid: rows
+// per band such that a band has at most kBandTiles tiles.  False when a single
+// row is wider than that or the grid is too tall for the segment records.
+bool chunked_bands(int tiles_x, int tiles_y, int &band_rows, int &n_bands) {
+    if (tiles_x <= 0 || tiles_y <= 0 || tiles_x > kBandTiles || tiles_y >= (1 << 14)) return false;
+    band_rows = kBandTiles / tiles_x;
+    if (band_rows > 8) band_rows = 8;  // more bands, more warps
+    n_bands = (tiles_y + band_rows - 1) / band_rows;
+    return true;
+}
+
+bool chunked_smem_ok(int tiles_x, int tiles_y) {
+    int r, b;
+    return chunked_bands(tiles_x, tiles_y, r, b);
+}
+
+// The tile id of every sorted pair position, from the ranges (one block per
+// tile).
+// Positions at or beyond n_out are not written.
+__global__ void expand_ranges_kernel(const uint2 *ranges, uint32_t ntiles, uint32_t *out, uint64_t n_out) {
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint2 r = ranges[t];
+        const uint64_t end = r.y < n_out ? r.y : n_out;
+        for (uint64_t i = (uint64_t)r.x + threadIdx.x; i < end; i += blockDim.x) out[i] = t;
+    }
+}
+
+cudaError_t launch_expand_ranges(const uint2 *ranges, int ntiles, uint32_t *out, uint64_t n_out, cudaStream_t s) {
+    if (ntiles <= 0 || n_out == 0) return cudaSuccess;
+    note_launch(), expand_ranges_kernel<<<ntiles < 65535 ? ntiles : 65535, 256, 0, s>>>(ranges, (uint32_t)ntiles, out, n_out);
+    return cudaGetLastError();
+}
+
+// Per-tile pair counts from the emitted tile ids: a shared-memory histogram
+// per block, merged into counts (zeroed by the caller) with global atomics.
+__global__ void __launch_bounds__(512) tile_count_kernel(const uint32_t *__restrict__ keys, uint64_t n_max,
+                                                         const uint64_t *n_dev, uint32_t ntiles, uint32_t *counts) {
+    extern __shared__ uint32_t s_hist[];
+    for (uint32_t t = threadIdx.x; t < ntiles; t += blockDim.x) s_hist[t] = 0u;
+    __syncthreads();
+    const uint64_t n = device_count(n_dev, n_max);
+    const uint64_t n4 = n / 4, stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);  // 256-byte aligned buffer
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const uint4 v = __ldcs(k4 + i);
+        if (v.x < ntiles) atomicAdd(&s_hist[v.x], 1u);
+        if (v.y < ntiles) atomicAdd(&s_hist[v.y], 1u);
+        if (v.z < ntiles) atomicAdd(&s_hist[v.z], 1u);
+        if (v.w < ntiles) atomicAdd(&s_hist[v.w], 1u);
+    }
+    for (uint64_t i = 4 * n4 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t k = keys[i];
+        if (k < ntiles) atomicAdd(&s_hist[k], 1u);
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t v = s_hist[t];
+        if (v) atomicAdd(&counts[t], v);
+    }
+}
+
+cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64_t *n_dev, int ntiles,
+                              uint32_t *counts, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * (size_t)ntiles, s);
+    if (e != cudaSuccess || n_max == 0 || ntiles == 0) return e;
+    const size_t smem = 4 * (size_t)ntiles;
+    static size_t set = 0;
+    if (smem > set) {
+        if ((e = cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        set = smem;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t blocks = (n_max / 4 + 511) / 512;
+    if (blocks > (uint64_t)sms * 2) blocks = (uint64_t)sms * 2;
+    if (blocks == 0) blocks = 1;
+    note_launch(), tile_count_kernel<<<(unsigned)blocks, 512, smem, s>>>(keys, n_max, n_dev, (uint32_t)ntiles, counts);
     return cudaGetLastError();
 }
 
@@ -381,29 +978,45 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
 // gives each tile's count; an exclusive scan over the global tile ids gives
 // the ranges of the tile-sorted pairs; the counts summed per digit give the
 // exclusive bucket offsets of every pass of the tile sort.  One block.
-__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, TileSet ts, TileOffsets off,
-                                                         uint2 *ranges, uint32_t *hist, int hist_stride, int rb,
-                                                         int passes, uint64_t capacity) {
+__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, const uint32_t *counts,
+                                                         TileSet ts, TileOffsets off, uint2 *ranges, uint32_t *hist,
+                                                         int hist_stride, int rb, int passes, uint64_t capacity) {
     extern __shared__ uint32_t sh_hist[];  // passes * 2^rb
     const int R = 1 << rb;
     for (int j = threadIdx.x; j < passes * R; j += blockDim.x) sh_hist[j] = 0u;
-    for (int c = 0; c < ts.n_cams; ++c) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int c = 0; c < (counts ? 0 : ts.n_cams); ++c) {
         const int tx = ts.cam[c].tiles_x, ty = ts.cam[c].tiles_y, stride = tx + 1;
         int *Dc = D + off.diff[c];
         const int *Sc = single + off.single[c];
-        for (int y = threadIdx.x; y < ty; y += blockDim.x) {
-            int run = 0;
-            for (int x = 0; x < tx; ++x) {
-                run += Dc[y * stride + x];
-                Dc[y * stride + x] = run;
+        // prefix along x: one warp per row, 32 cells at a time
+        for (int y = wid; y < ty; y += nwarps) {
+            int carry = 0;
+            for (int x0 = 0; x0 < tx; x0 += 32) {
+                const int x = x0 + lane;
+                const int v = x < tx ? Dc[y * stride + x] : 0;
+                const int incl = warp_incl_scan(v) + carry;
+                if (x < tx) Dc[y * stride + x] = incl;
+                carry = __shfl_sync(0xffffffffu, incl, 31);
             }
         }
         __syncthreads();
+        // prefix along y: one thread per column, eight rows loaded at a time
         for (int x = threadIdx.x; x < tx; x += blockDim.x) {
             int run = 0;
-            for (int y = 0; y < ty; ++y) {
-                run += Dc[y * stride + x];
-                Dc[y * stride + x] = run + Sc[y * tx + x];
+            for (int y0 = 0; y0 < ty; y0 += 8) {
+                int v[8], sg[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const bool in = y0 + k < ty;
+                    v[k] = in ? Dc[(y0 + k) * stride + x] : 0;
+                    sg[k] = in ? Sc[(y0 + k) * tx + x] : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    run += v[k];
+                    if (y0 + k < ty) Dc[(y0 + k) * stride + x] = run + sg[k];
+                }
             }
         }
         __syncthreads();
@@ -413,6 +1026,7 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
     const int per = (ntiles + blockDim.x - 1) / blockDim.x;
     const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
     auto count_of = [&](int t) -> uint32_t {
+        if (counts) return counts[t];
         const int c = camera_of(ts, (uint32_t)t);
         const int lt = t - (int)ts.cam[c].tile_base, tx = ts.cam[c].tiles_x;
         return (uint32_t)D[off.diff[c] + (lt / tx) * (tx + 1) + lt % tx];
@@ -448,16 +1062,16 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
     }
 }
 
-cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileSet &ts, const uint32_t *diff_off,
-                             const uint32_t *single_off, uint2 *ranges, uint32_t *hist, int hist_stride,
-                             int digit_bits, int passes, uint64_t capacity, cudaStream_t s) {
+cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint32_t *counts, const TileSet &ts,
+                             const uint32_t *diff_off, const uint32_t *single_off, uint2 *ranges, uint32_t *hist,
+                             int hist_stride, int digit_bits, int passes, uint64_t capacity, cudaStream_t s) {
     TileOffsets off;
     for (int c = 0; c < kMaxGroupCams; ++c) {
         off.diff[c] = c < ts.n_cams ? diff_off[c] : 0u;
         off.single[c] = c < ts.n_cams ? single_off[c] : 0u;
     }
     const size_t smem = (size_t)passes * ((size_t)1 << digit_bits) * 4;
-    tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, ts, off, ranges, hist, hist_stride, digit_bits,
+    note_launch(), tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, counts, ts, off, ranges, hist, hist_stride, digit_bits,
                                            passes, capacity);
     return cudaGetLastError();
 }

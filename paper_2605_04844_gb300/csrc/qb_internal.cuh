@@ -37,12 +37,13 @@ struct CamDev {
 
 // Workspace offsets (bytes) of a frame; all 256-byte aligned.
 struct Layout {
-    size_t xy, conic_o, rgbd, box, r3, meta, counts, offsets;
+    size_t xy, conic_o, rgbd, box, r3, meta, counts, offsets, segs, segs_d;
     size_t scan_part;
     size_t keys0, keys1, vals0, vals1;
     size_t sort_scratch, sort_scratch_bytes;
     size_t dkeys0, dkeys1, dvals0, dvals1, dsort_scratch;  // depth order of the Gaussians
     size_t ranges, tfinal, ncontrib, neval;
+    size_t chunk_start, chunk_cnt, chunk_part, chunk_total;  // chunked placement tables
     size_t tile_diff;  // (tiles_y+1) x (tiles_x+1) int difference array
     size_t tile_single;  // tiles ints: pair counts of single-tile Gaussians
     size_t gscreen;  // [n][9] screen-space gradients
@@ -54,6 +55,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Sets the message qb_last_error() returns on the calling thread.
 void set_last_error(const char *msg);
+// Counts one kernel launch of the library (qb_kernel_launches).
+void note_launch();
 
 // ---- sort -------------------------------------------------------------------
 size_t sort_scratch_bytes(uint64_t n, int end_bit, int digit_bits);
@@ -72,6 +75,20 @@ cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint3
                        bool hist_ready = false);
 uint32_t *sort_hist_table(void *scratch);
 int sort_hist_stride();
+// Pieces of the depth-first tile sort.  The look-back words of pass p are laid
+// out for n_cap pairs; sort_clear zeroes the tile counters and look-back words
+// of passes [first_pass, end_pass).
+uint32_t *sort_lookback(void *scratch, uint64_t n_cap, int digit_bits, int pass);
+uint32_t *sort_counter(void *scratch, int pass);
+cudaError_t sort_clear(void *scratch, uint64_t n_cap, int digit_bits, int first_pass, int end_pass,
+                       cudaStream_t s);
+// Passes [first_pass, passes) of the tile sort: pass p writes buffer A when
+// passes - 1 - p is even, else B, reading the other; the last pass writes
+// values only (into A).
+cudaError_t tile_sort_passes(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, uint64_t n_cap, uint64_t n_max,
+                             const uint64_t *n_dev, int passes, int first_pass, int digit_bits, void *scratch,
+                             uint32_t *err, cudaStream_t s);
+inline bool pass_writes_a(int passes, int p) { return ((passes - 1 - p) & 1) == 0; }
 
 // ---- device helpers -----------------------------------------------------------
 // Exponents below this give alpha = o e^power < (1/255) e^-0.001: the 1e-3
@@ -215,10 +232,18 @@ struct QSeg {
     int nl, len;  // lines in the run, interval length
 };
 
+// The runs are found in order and stored in fixed slots (so the array stays
+// in registers): slot k holds the k-th run, an empty one (no sub-box overlaps
+// its lines) with nl = len = 0.  The lines [s0, s1] have at most six interior
+// breakpoints (each sub-box begins or ends at most once), so seven slots hold
+// every run.  Returns the number of slots used.
 __device__ __forceinline__ int qpass_segments(const QPass &qp, QSeg seg[7]) {
-    int ns = 0;
+    int used = 0;
     int cur = qp.s0;
-    while (cur <= qp.s1 && ns < 7) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        seg[k] = QSeg{0, 0, 0, 0};
+        if (cur > qp.s1) continue;
         int next = qp.s1 + 1;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -230,11 +255,14 @@ __device__ __forceinline__ int qpass_segments(const QPass &qp, QSeg seg[7]) {
         }
         int lo, hi;
         qpass_line(qp, cur, lo, hi);
-        if (hi >= lo) seg[ns++] = QSeg{cur, lo, next - cur, hi - lo + 1};
+        if (hi >= lo) seg[k] = QSeg{cur, lo, next - cur, hi - lo + 1};
+        used = k + 1;
         cur = next;
     }
-    return ns;
+    return used;
 }
+
+__device__ __forceinline__ bool seg_empty(const QSeg &g) { return g.nl <= 0 || g.len <= 0; }
 
 __device__ __forceinline__ uint32_t qpass_count(const Rect rects[4]) {
     QPass qp;

@@ -30,7 +30,15 @@ struct PreArgs {
     int *tile_diff;    // per camera [(tiles_y+1)][(tiles_x+1)] difference array of pair counts, or null
     int *tile_single;  // per camera [tiles] pair counts of single-tile Gaussians
     uint32_t diff_off[kMaxGroupCams], single_off[kMaxGroupCams];
+    uint4 *segs;       // [records][4] QPass segment records (pack_segments), or null
 };
+
+// A Gaussian's QPass traversal as at most seven segments, packed in 16 words
+// (four uint4): word 0 = segment count | column flag << 3 | first tile row
+// << 4 | last tile row << 18; segment k in words 1 + 2k (first line | first
+// cell << 16) and 2 + 2k (lines | cells << 16).
+// Only the first ceil((1 + 2 ns) / 4) uint4 are written and read.
+__device__ __forceinline__ int seg_chunks(int ns) { return (1 + 2 * ns + 3) >> 2; }
 
 // Image geometry of one camera in a set of cameras rendered together.  Tile
 // ids are global over the set (camera c owns [tile_base, tile_base + tiles));
@@ -70,6 +78,7 @@ struct EmitArgs {
     const float4 *rgbd;
     const uint32_t *counts;   // by Gaussian
     const uint32_t *offsets;  // by emission position
+    const uint4 *segs;        // QPass segment records from the preprocess, or null (recomputed)
     uint32_t *vals;
     const uint64_t *n_pairs;
     uint64_t n_pairs_host;  // P when the host knows it, else UINT64_MAX
@@ -78,6 +87,31 @@ struct EmitArgs {
     bool clamp3s;
     uint32_t *err;
     TileSet ts;  // camera of record r is r / n_per_cam
+};
+
+// Chunked counting placement of the depth-ordered pairs (one camera).
+constexpr uint32_t kChunkPairs = 65536;     // pairs per chunk (K)
+constexpr uint32_t kChunkSegs = 32;         // chunk segments of the two-level scan
+constexpr size_t kChunkMaxSmem = 96 * 1024;  // shared memory bound of its kernels
+
+constexpr int kBandTiles = 4096;  // tiles of one band at most (band-local keys < 2^12)
+
+struct ChunkArgs {
+    int tiles_x, tiles_y;
+    int band_rows, n_bands;  // tile rows per band, bands
+    int band_diff_ints;      // (band_rows + 1) x (tiles_x + 1)
+    int band_words;          // per-warp shared words of the placement: cursor (band tiles, rounded to 4)
+    uint32_t n_chunks, chunk_pairs, n_segs, chunks_per_seg;
+    const uint32_t *perm;    // emission order -> Gaussian
+    const uint32_t *counts;  // by Gaussian
+    const uint4 *segs;       // QPass segment records by Gaussian
+    uint4 *segs_d;           // the same records in emission (depth) order
+    const uint64_t *n_pairs;
+    uint64_t capacity;
+    uint32_t *start;  // [n_chunks + 1]
+    uint32_t *cnt;    // [n_chunks][tiles]: counts, then first positions
+    uint32_t *part;   // [n_segs][tiles]
+    uint32_t *total;  // [tiles]
 };
 
 struct RenderArgs {
@@ -130,12 +164,27 @@ cudaError_t launch_depth_keys(int n, const float4 *rgbd, const uint32_t *counts,
                               cudaStream_t s);
 template <typename KeyT>
 cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s);
+// K3 fused with the first pass of the depth-first tile sort (digit bits
+// [0, digit_bits) of the tile id); write_keys false when it is the only pass.
+cudaError_t launch_emit_sweep(const EmitArgs &a, int digit_bits, bool write_keys, uint32_t *kout, uint32_t *vout,
+                              const uint32_t *bin_off, uint32_t *lookback, uint32_t *counter, cudaStream_t s);
+// Counts, scans and places the pairs (writes e.vals and the ranges).
+cudaError_t launch_chunked(const EmitArgs &e, const ChunkArgs &a, uint2 *ranges, cudaStream_t s);
+bool chunked_smem_ok(int tiles_x, int tiles_y);
+bool chunked_bands(int tiles_x, int tiles_y, int &band_rows, int &n_bands);
+cudaError_t launch_expand_ranges(const uint2 *ranges, int ntiles, uint32_t *out, uint64_t n_out, cudaStream_t s);
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges, int ntiles,
                           cudaStream_t s);
-cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileSet &ts, const uint32_t *diff_off,
-                             const uint32_t *single_off, uint2 *ranges, uint32_t *hist, int hist_stride,
-                             int digit_bits, int passes, uint64_t capacity, cudaStream_t s);
+// Ranges and every tile-sort pass's bucket offsets from per-tile counts: the
+// preprocess's difference arrays (counts null) or a count array.
+cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint32_t *counts, const TileSet &ts,
+                             const uint32_t *diff_off, const uint32_t *single_off, uint2 *ranges, uint32_t *hist,
+                             int hist_stride, int digit_bits, int passes, uint64_t capacity, cudaStream_t s);
+// Per-tile counts of n tile ids (counts zeroed here); ntiles <= kTileCountMax.
+constexpr int kTileCountMax = 24576;
+cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64_t *n_dev, int ntiles,
+                              uint32_t *counts, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs &a, int batch, cudaStream_t s);
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s);

@@ -90,18 +90,50 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
         QSeg seg[7];
         const int ns = qpass_segments(qp, seg);
         // QPass count: the lines of each run of equal intervals times its length
-        for (int q = 0; q < ns; ++q) cnt += (uint32_t)(seg[q].nl * seg[q].len);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) cnt += (uint32_t)(seg[q].nl * seg[q].len);
+        if (a.segs && cnt > 0u) {
+            // the segments, for the emit (which then skips the box and QPass setup)
+            uint32_t w[16];
+            int ylo = 1 << 14, yhi = -1;  // tile rows the segments cover
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                if (seg_empty(seg[q])) continue;
+                const int a0 = qp.columns ? seg[q].lo : seg[q].s0;
+                const int a1 = a0 + (qp.columns ? seg[q].len : seg[q].nl) - 1;
+                ylo = min(ylo, a0);
+                yhi = max(yhi, a1);
+            }
+            w[0] = (uint32_t)ns | ((uint32_t)qp.columns << 3) | ((uint32_t)ylo << 4) | ((uint32_t)yhi << 18);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                w[1 + 2 * q] = q < ns ? (uint32_t)seg[q].s0 | ((uint32_t)seg[q].lo << 16) : 0u;
+                w[2 + 2 * q] = q < ns ? (uint32_t)seg[q].nl | ((uint32_t)seg[q].len << 16) : 0u;
+            }
+            w[15] = 0u;
+            uint4 *dst = a.segs + 4 * o;
+            const int nc = seg_chunks(ns);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nc) dst[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+        }
         const int tiles_x = (cam.W + kTile - 1) >> kTileShift;
         if (a.tile_diff && cnt == 1u) {
             // one tile (the common case): count it directly
-            const int t = qp.columns ? seg[0].lo * tiles_x + seg[0].s0 : seg[0].s0 * tiles_x + seg[0].lo;
+            int t = 0;
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+                if (!seg_empty(seg[q]))
+                    t = qp.columns ? seg[q].lo * tiles_x + seg[q].s0 : seg[q].s0 * tiles_x + seg[q].lo;
             atomicAdd(a.tile_single + a.single_off[ci] + t, 1);
         } else if (a.tile_diff) {
             // per-tile pair counts as a 2D difference array: +1/-1 at the corners
             // of every rectangle of the Gaussian's tile set
             const int stride = tiles_x + 1;
             int *D = a.tile_diff + a.diff_off[ci];
-            for (int q = 0; q < ns; ++q) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                if (seg_empty(seg[q])) continue;
                 const int l0 = seg[q].s0, l1 = seg[q].s0 + seg[q].nl - 1;
                 const int u0 = seg[q].lo, u1 = seg[q].lo + seg[q].len - 1;
                 const int x0 = qp.columns ? l0 : u0, x1 = qp.columns ? l1 : u1;
@@ -128,10 +160,10 @@ cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     dim3 grid((a.n + 255) / 256, a.cams.n_cams), block(256);
     switch (deg) {
-    case 0: preprocess_kernel<0><<<grid, block, 0, s>>>(a); break;
-    case 1: preprocess_kernel<1><<<grid, block, 0, s>>>(a); break;
-    case 2: preprocess_kernel<2><<<grid, block, 0, s>>>(a); break;
-    default: preprocess_kernel<3><<<grid, block, 0, s>>>(a); break;
+    case 0: note_launch(), preprocess_kernel<0><<<grid, block, 0, s>>>(a); break;
+    case 1: note_launch(), preprocess_kernel<1><<<grid, block, 0, s>>>(a); break;
+    case 2: note_launch(), preprocess_kernel<2><<<grid, block, 0, s>>>(a); break;
+    default: note_launch(), preprocess_kernel<3><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

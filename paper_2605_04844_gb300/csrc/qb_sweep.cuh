@@ -1,0 +1,268 @@
+// qb_sweep.cuh -- the body of one digit pass of the onesweep radix sort
+// (SortPairs, Sec. 2), shared by the plain pass kernel (qb_sort.cu) and the
+// QPass emit that performs the tile sort's first pass itself (qb_binning.cu).
+//
+// A block owns one tile of 4096 consecutive input positions; its keys arrive
+// in registers, warp-striped (item k of lane l of warp w is position
+// 256 w + 32 k + l of the tile).  The block counts its digits (shared
+// atomics, order-free), publishes the counts and looks back over earlier
+// tiles for their running totals, ranks its keys per warp in input order,
+// and scatters keys then values through shared memory so that runs of equal
+// digits leave as contiguous stores.  Tile indices are taken from an atomic
+// counter in launch order, so every earlier tile belongs to a block that is
+// already running.  Every look-back spin is bounded; on expiry it raises
+// kErrTimeout and still publishes, so no block waits forever.
+#pragma once
+
+#include "qb_kernels.cuh"
+
+namespace qb {
+
+constexpr int kSortBlock = 512;
+constexpr int kSortWarps = kSortBlock / 32;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortBlock * kSortItems;  // 4096 keys per block
+constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookWindow = 8;  // status words fetched per look-back step
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagIncl = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1u;
+constexpr int kHistStride = 1 << kMaxDigitBits;  // per-pass stride of the histogram table
+// scratch: [bucket offset table: kMaxPasses x kHistStride u32][tile counters:
+// kMaxPasses u32, padded to 256 B][look-back words: passes x tiles x 2^RB u32]
+constexpr size_t kSortCounters = (size_t)kMaxPasses * kHistStride * 4;
+constexpr size_t kSortHeader = kSortCounters + 256;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Elements to sort: the device count when given, treated as zero when it
+// exceeds the buffers (an overflow the emit has already flagged).
+__device__ __forceinline__ uint64_t device_count(const uint64_t *n_dev, uint64_t n_max) {
+    if (!n_dev) return n_max;
+    const uint64_t n = *n_dev;
+    return n > n_max ? 0 : n;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < nw ? ws[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t u = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += u;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    uint32_t before = wid > 0 ? ws[wid - 1] : 0u;
+    *total = ws[nw - 1];
+    __syncthreads();
+    return incl - v + before;
+}
+
+// Shared memory of one pass: the scatter buffer (keys, then values), per-warp
+// digit counters, and per-digit global base, local start and tile count.
+template <int RB, typename KeyT>
+constexpr size_t sweep_smem() {
+    return (size_t)kSortTile * sizeof(KeyT) + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)3 * (1 << RB) * 4;
+}
+
+// One pass over the tile `tile` (positions [tbase, tbase + 4096) of n).
+// bin_off: the pass's exclusive bucket offsets; lookback: the pass's status
+// words [tiles][2^RB].  With WRITE_KEYS false only the values are written
+// (the last pass, whose keys are implied by the per-tile ranges).
+template <int RB, typename KeyT, bool WRITE_KEYS>
+__device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const uint32_t (&val)[kSortItems],
+                                           uint64_t n, uint64_t tbase, uint32_t tile,
+                                           const uint32_t *__restrict__ bin_off, uint32_t *lookback, int shift,
+                                           uint32_t *err, KeyT *__restrict__ kout, uint32_t *__restrict__ vout,
+                                           uint8_t *smem) {
+    constexpr int R = 1 << RB;
+    constexpr uint32_t MASK = R - 1;
+    constexpr int PER = (R + kSortBlock - 1) / kSortBlock;
+    KeyT *s_keys = reinterpret_cast<KeyT *>(smem);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem);
+    uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem + (size_t)kSortTile * sizeof(KeyT));
+    uint32_t *s_gbase = reinterpret_cast<uint32_t *>(s_whist + kSortWarps * R);
+    uint32_t *s_lstart = s_gbase + R;
+    uint32_t *s_bcount = s_lstart + R;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int j = tid; j < kSortWarps * R / 2; j += kSortBlock) reinterpret_cast<uint32_t *>(s_whist)[j] = 0u;
+    for (int j = tid; j < R; j += kSortBlock) s_bcount[j] = 0u;
+    __syncthreads();
+    const uint64_t wbase = tbase + (uint64_t)wid * (32 * kSortItems);
+    uint32_t rank[kSortItems];
+
+    // ---- early digit counts of the tile ----
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k)
+        if (wbase + 32 * k + lane < n) atomicAdd(&s_bcount[(uint32_t)(key[k] >> shift) & MASK], 1u);
+    __syncthreads();
+
+    // ---- publish, look back, publish the inclusive prefix ----
+    // One status word per (tile, digit): a 2-bit flag (aggregate = the tile's
+    // own count, inclusive = running total through the tile) and a 30-bit
+    // count.  Each thread walks back for its digits, kLookWindow words at a
+    // time (their addresses do not depend on what is read), adding aggregates
+    // until it meets an inclusive total; when the next word is not yet
+    // published it polls that word alone, sleeping between polls.
+    uint32_t cnt[PER], tsum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        int d = tid * PER + j;
+        cnt[j] = d < R ? s_bcount[d] : 0u;
+        tsum += cnt[j];
+    }
+    uint32_t *lb = lookback + (size_t)tile * R;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        int d = tid * PER + j;
+        if (d < R) st_relaxed(lb + d, (tile == 0 ? kFlagIncl : kFlagAgg) | cnt[j]);
+    }
+    uint32_t btotal;
+    uint32_t run = block_excl_scan_u32(tsum, &btotal);  // contains __syncthreads
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        int d = tid * PER + j;
+        if (d >= R) continue;
+        s_lstart[d] = run;
+        run += cnt[j];
+        uint32_t acc = 0;
+        if (tile > 0) {
+            int64_t t = (int64_t)tile - 1;
+            int spins = 0;
+            bool done = false;
+            while (!done && t >= 0) {
+                uint32_t sv[kLookWindow];
+#pragma unroll
+                for (int w = 0; w < kLookWindow; ++w)
+                    sv[w] = (t - w >= 0) ? ld_relaxed(lookback + (size_t)(t - w) * R + d) : kFlagIncl;
+                int used = 0;
+#pragma unroll
+                for (int w = 0; w < kLookWindow; ++w) {
+                    if (done || used < w) continue;  // stopped at an unpublished word
+                    const uint32_t f = sv[w] & ~kCountMask;
+                    if (f == 0u) continue;
+                    acc += sv[w] & kCountMask;
+                    used = w + 1;
+                    if (f == kFlagIncl) done = true;
+                }
+                t -= used;
+                if (!done && used == 0) {
+                    // the nearest earlier tile has not published this digit yet
+                    unsigned ns = 32;
+                    while ((ld_relaxed(lookback + (size_t)t * R + d) & ~kCountMask) == 0u) {
+                        if (++spins > kSpinLimit) break;
+                        __nanosleep(ns);
+                        ns = ns < 512 ? 2 * ns : 512;
+                    }
+                    if (spins > kSpinLimit) {
+                        atomicOr(err, kErrTimeout);
+                        break;
+                    }
+                }
+            }
+            st_relaxed(lb + d, kFlagIncl | ((acc + cnt[j]) & kCountMask));
+        }
+        s_gbase[d] = bin_off[d] + acc;
+    }
+    __syncthreads();
+
+    // ---- rank within the warp, in original order ----
+    // Lanes holding the same digit are found with one ballot per digit bit.
+    uint16_t *wh = s_whist + wid * R;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const bool valid = wbase + 32 * k + lane < n;
+        const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & MASK : (uint32_t)R;
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        uint32_t peers = valid ? vmask : ~vmask;
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+        const uint32_t pre = valid ? (uint32_t)wh[d] : 0u;
+        const uint32_t lower = __popc(peers & lt);
+        __syncwarp();
+        if (valid && lower == 0) wh[d] = (uint16_t)(pre + __popc(peers));
+        __syncwarp();
+        rank[k] = pre + lower;
+    }
+    __syncthreads();
+
+    // ---- per digit: exclusive prefix over the warps ----
+    for (int d = tid; d < R; d += kSortBlock) {
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t c = s_whist[w * R + d];
+            s_whist[w * R + d] = (uint16_t)r;
+            r += c;
+        }
+    }
+    __syncthreads();
+
+    // ---- keys: scatter to block order in shared memory, then out ----
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        if (wbase + 32 * k + lane < n) {
+            uint32_t d = (uint32_t)(key[k] >> shift) & MASK;
+            uint32_t lr = s_lstart[d] + s_whist[wid * R + d] + rank[k];
+            s_keys[lr] = key[k];
+            rank[k] = lr;
+        }
+    }
+    __syncthreads();
+    const uint32_t tcount = (uint32_t)min((uint64_t)kSortTile, n - tbase);
+    uint32_t dest[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        uint32_t j = tid + k * kSortBlock;
+        if (j < tcount) {
+            const KeyT kk = s_keys[j];
+            uint32_t d = (uint32_t)(kk >> shift) & MASK;
+            dest[k] = s_gbase[d] + (j - s_lstart[d]);
+            if (WRITE_KEYS && dest[k] < n) kout[dest[k]] = kk;  // dest >= n only after a look-back timeout
+        }
+    }
+    __syncthreads();
+    // ---- values through the same permutation ----
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k)
+        if (wbase + 32 * k + lane < n) s_vals[rank[k]] = val[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        uint32_t j = tid + k * kSortBlock;
+        if (j < tcount && dest[k] < n) vout[dest[k]] = s_vals[j];
+    }
+}
+
+}  // namespace qb

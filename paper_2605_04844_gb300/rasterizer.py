@@ -66,6 +66,9 @@ def scene_struct(scene) -> N.QbScene:
     return s
 
 
+SORT_MODES = {"depth_first": 0, "full_key": 1, "chunked": 2}
+
+
 class Frame:
     """One rasterisation frame: a workspace plus the qb_frame handle."""
 
@@ -83,13 +86,15 @@ class Frame:
         N.qb_frame_init(self.frame, self.n, self.width, self.height, self.pair_capacity, self.ws, stream)
 
     # -- configuration ------------------------------------------------------
-    def set_tuning(self, digit_bits=None, render_batch=None, sort_mode=None):
+    def set_tuning(self, digit_bits=None, render_batch=None, sort_mode=None, emit_fused=None):
         if digit_bits is not None:
             self.frame.sort_digit_bits = int(digit_bits)
         if sort_mode is not None:
-            self.frame.sort_mode = {"depth_first": 0, "full_key": 1}.get(sort_mode, sort_mode)
+            self.frame.sort_mode = SORT_MODES.get(sort_mode, sort_mode)
         if render_batch is not None:
             self.frame.render_batch = int(render_batch)
+        if emit_fused is not None:
+            self.frame.emit_fused = int(bool(emit_fused))
 
     # -- stages -----------------------------------------------------------------
     def preprocess(self, scene_s: N.QbScene, cam_s: N.QbCamera, mode):
@@ -116,6 +121,13 @@ class Frame:
         return None if v == 2 ** 64 - 1 else int(v)
 
     # -- inspection ----------------------------------------------------------------
+    def sorted_tile_keys(self, n_pairs=None):
+        """The tile id of every sorted pair (from the per-tile ranges)."""
+        P = n_pairs if n_pairs is not None else (self.n_pairs or 0)
+        out = torch.empty(P, dtype=torch.int32, device=self.ws.device)
+        N.qb_frame_tile_keys(self.frame, out, self.stream)
+        return out
+
     def _view(self, p, dtype, shape):
         off = p - self.ws.data_ptr()
         nbytes = int(math.prod(shape)) * torch.empty((), dtype=dtype).element_size()
@@ -136,7 +148,7 @@ class Frame:
             "counts": self._view(a.counts, torch.int32, (n,)),
             "offsets": self._view(a.offsets, torch.int32, (n,)),
             "keys": self._view(a.keys, torch.int64, (P,)),
-            "tile_keys": self._view(a.tile_keys, torch.int32, (P,)),
+            "tile_keys": self.sorted_tile_keys(P) if self.frame.stage >= 3 else self._view(a.tile_keys, torch.int32, (P,)),
             "vals": self._view(a.vals, torch.int32, (P,)),
             "depth_order": self._view(a.depth_order, torch.int32, (n,)),
             "ranges": self._view(a.ranges, torch.int32, (tiles, 2)),
@@ -153,7 +165,7 @@ def estimate_capacity(n, width, height):
 
 
 def forward(scene, cam, mode="quadbox", bg=None, frame: Frame | None = None, digit_bits=8, capacity=None,
-            sort_mode="depth_first"):
+            sort_mode="depth_first", emit_fused=False):
     """Full forward pass.  Returns (image [3,H,W], frame).  Grows the pair
     buffer when the tile pairs exceed it (the count is read back once)."""
     scene_s = scene_struct(scene)
@@ -161,7 +173,7 @@ def forward(scene, cam, mode="quadbox", bg=None, frame: Frame | None = None, dig
     n, W, H = scene_s.n, cam_s.width, cam_s.height
     if frame is None or frame.n != n or frame.width != W or frame.height != H:
         frame = Frame(n, W, H, capacity or estimate_capacity(n, W, H))
-    frame.set_tuning(digit_bits=digit_bits, sort_mode=sort_mode)
+    frame.set_tuning(digit_bits=digit_bits, sort_mode=sort_mode, emit_fused=emit_fused)
     while True:
         frame.preprocess(scene_s, cam_s, mode)
         try:
@@ -170,7 +182,7 @@ def forward(scene, cam, mode="quadbox", bg=None, frame: Frame | None = None, dig
         except N.QbCapacityError:
             P = _read_pairs(frame)
             frame = Frame(n, W, H, min(2 ** 30, int(P * 1.25) + 1024))
-            frame.set_tuning(digit_bits=digit_bits, sort_mode=sort_mode)
+            frame.set_tuning(digit_bits=digit_bits, sort_mode=sort_mode, emit_fused=emit_fused)
     frame.sort()
     img = frame.render(bg)
     return img, frame

@@ -21,9 +21,12 @@ def f64(scene):
 
 
 def run_forward(scene, cam, mode="quadbox", bg=None, digit_bits=8, capacity=None, sort_mode="depth_first"):
+    """sort_mode: a rasterizer sort mode, or "depth_first_fused" (depth-first
+    with the emit fused with the first tile-sort pass)."""
     from paper_2605_04844_gb300 import rasterizer as R
+    fused = sort_mode == "depth_first_fused"
     img, fr = R.forward(to_device(scene), cam, mode, bg=bg, digit_bits=digit_bits, capacity=capacity,
-                        sort_mode=sort_mode)
+                        sort_mode="depth_first" if fused else sort_mode, emit_fused=fused)
     import torch
     torch.cuda.synchronize()
     fr.check()

@@ -64,7 +64,7 @@ def test_preprocess_parity(maker):
 
 @pytest.mark.parametrize("name,mode", MODES)
 @pytest.mark.parametrize("clamp", [True, False])
-@pytest.mark.parametrize("sort_mode", ["depth_first", "full_key"])
+@pytest.mark.parametrize("sort_mode", ["depth_first", "depth_first_fused", "full_key", "chunked"])
 def test_keys_and_ranges_bit_exact(name, mode, clamp, sort_mode):
     scene, cam = c2_small()
     W, H = cam["width"], cam["height"]
@@ -80,7 +80,7 @@ def test_keys_and_ranges_bit_exact(name, mode, clamp, sort_mode):
 
 
 @pytest.mark.parametrize("digit_bits", [8, 9, 10, 11])
-@pytest.mark.parametrize("sort_mode", ["depth_first", "full_key"])
+@pytest.mark.parametrize("sort_mode", ["depth_first", "depth_first_fused", "full_key", "chunked"])
 def test_keys_bit_exact_all_digit_widths(digit_bits, sort_mode):
     scene, cam = c1_small()
     img, fr, A = run_forward(scene, cam, "quadbox", digit_bits=digit_bits, sort_mode=sort_mode)
@@ -100,10 +100,29 @@ def test_depth_order_is_stable_depth_sort():
 def test_sort_modes_identical_images():
     scene, cam = c2_small()
     a = run_forward(scene, cam, "quadbox", sort_mode="depth_first")
-    b = run_forward(scene, cam, "quadbox", sort_mode="full_key")
-    np.testing.assert_array_equal(a[0], b[0])
-    np.testing.assert_array_equal(a[2]["vals"], b[2]["vals"])
-    np.testing.assert_array_equal(a[2]["ranges"], b[2]["ranges"])
+    for other in ("depth_first_fused", "full_key", "chunked"):
+        b = run_forward(scene, cam, "quadbox", sort_mode=other)
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[2]["vals"], b[2]["vals"])
+        np.testing.assert_array_equal(a[2]["ranges"], b[2]["ranges"])
+
+
+@pytest.mark.parametrize("mode", ["quadbox", "aabb3s"])
+def test_chunked_placement_many_chunks(mode):
+    """Millions of pairs over many 65536-pair chunks and a ragged last
+    chunk: keys and ranges bit-exact against the oracle's traversal of the
+    GPU machines, values identical to the radix tile sort."""
+    cam = synth.pinhole(640, 480)
+    scene = synth.scene_blobs(300_000, 1077, cam, deg=0)
+    img_c, fr_c, C = run_forward(scene, cam, mode, sort_mode="chunked")
+    assert fr_c.n_pairs > 8 * 65536 and fr_c.n_pairs % 65536 != 0
+    o = oracle_keys_from_gpu_boxes(C, O.QUADBOX if mode == "quadbox" else O.AABB3S, True, 640, 480)
+    np.testing.assert_array_equal(C["full_keys"], o["keys"])
+    np.testing.assert_array_equal(C["vals"].astype(np.uint32), o["vals"])
+    np.testing.assert_array_equal(C["ranges"].astype(np.int64), o["ranges"])
+    img_d, fr_d, D = run_forward(scene, cam, mode, sort_mode="depth_first")
+    np.testing.assert_array_equal(C["vals"], D["vals"])
+    np.testing.assert_array_equal(img_c, img_d)
 
 
 @pytest.mark.parametrize("maker", [c1_small, c2_small])
@@ -135,12 +154,13 @@ def test_quadbox_fewer_pairs_than_aabb():
     assert P["dualbox"] <= P["quadbox"]
 
 
-def test_ragged_image_and_tiny_scenes():
+@pytest.mark.parametrize("sort_mode", ["depth_first", "depth_first_fused", "full_key", "chunked"])
+def test_ragged_image_and_tiny_scenes(sort_mode):
     # image sizes that are not multiples of 16, a one-pixel image, one Gaussian, no Gaussian
     for (W, H, n) in [(37, 23, 300), (1, 1, 5), (17, 16, 1), (64, 48, 0)]:
         cam = synth.pinhole(W, H)
         scene = synth.scene_uniform(n, 5 + W, cam, depth=(1.0, 4.0), logscale=(-1.5, 0.5))
-        img, fr, A = run_forward(scene, cam, "quadbox", bg=(0.2, 0.3, 0.4))
+        img, fr, A = run_forward(scene, cam, "quadbox", bg=(0.2, 0.3, 0.4), sort_mode=sort_mode)
         ref = O.image(f64(scene), cam, O.QUADBOX, bg=(0.2, 0.3, 0.4))
         ok, st = image_parity(img, ref)
         assert ok, (W, H, n, st)
@@ -149,25 +169,28 @@ def test_ragged_image_and_tiny_scenes():
             np.testing.assert_array_equal(A["full_keys"], o["keys"])
 
 
-def test_huge_gaussian_covering_everything():
+@pytest.mark.parametrize("sort_mode", ["depth_first", "depth_first_fused", "chunked"])
+def test_huge_gaussian_covering_everything(sort_mode):
     cam = synth.pinhole(300, 200)
     scene = synth.scene_uniform(50, 9, cam, depth=(1.0, 3.0), logscale=(-3.0, 0.3))
     scene["scales"][0] = [1.5, -0.5, 0.2]  # several hundred pixels
     scene["opacities"][0] = 3.0
-    img, fr, A = run_forward(scene, cam, "quadbox")
+    img, fr, A = run_forward(scene, cam, "quadbox", sort_mode=sort_mode)
     o = oracle_keys_from_gpu_boxes(A, O.QUADBOX, True, 300, 200)
     np.testing.assert_array_equal(A["full_keys"], o["keys"])
     ok, st = image_parity(img, O.image(f64(scene), cam, O.QUADBOX))
     assert ok, st
 
 
-def test_capacity_overflow_is_reported_not_written():
+@pytest.mark.parametrize("sort_mode", ["depth_first", "depth_first_fused", "chunked"])
+def test_capacity_overflow_is_reported_not_written(sort_mode):
     import torch
     from paper_2605_04844_gb300 import _native as N
     from paper_2605_04844_gb300 import rasterizer as R
     scene, cam = c1_small(2000, 128, 128)
     sd = to_device(scene)
     fr = R.Frame(2000, 128, 128, pair_capacity=64)
+    fr.set_tuning(sort_mode=sort_mode.replace("_fused", ""), emit_fused=sort_mode.endswith("_fused"))
     s, c = R.scene_struct(sd), R.camera_struct(cam)
     fr.preprocess(s, c, "quadbox")
     with pytest.raises(N.QbCapacityError):
@@ -181,12 +204,18 @@ def test_capacity_overflow_is_reported_not_written():
         fr.check()
     assert torch.equal(fr.arrays(n_pairs=64)["keys"], keys_before)
     fr.check()  # flags were cleared
+    # and the render after an overflowed, unsynchronised emit sees empty tiles
+    fr.sort()
+    img = fr.render((0.25, 0.5, 0.75))
+    torch.cuda.synchronize()
+    assert torch.equal(img[0], torch.full_like(img[0], 0.25))
     # the forward helper grows the buffer and succeeds
     img, fr2 = R.forward(sd, cam, "quadbox", capacity=64)
     assert fr2.pair_capacity >= fr2.n_pairs
 
 
-def test_unsynchronised_pipeline_matches_synchronised():
+@pytest.mark.parametrize("sort_mode", ["depth_first", "depth_first_fused", "chunked"])
+def test_unsynchronised_pipeline_matches_synchronised(sort_mode):
     """qb_bin_emit without the host read-back (capacity-sized sort) gives the
     same image and keys."""
     import torch
@@ -194,7 +223,8 @@ def test_unsynchronised_pipeline_matches_synchronised():
     scene, cam = c2_small()
     img_a, fr_a, A = run_forward(scene, cam, "quadbox")
     sd = to_device(scene)
-    fr = R.Frame(len(scene["opacities"]), cam["width"], cam["height"], pair_capacity=fr_a.n_pairs + 5000)
+    fr = R.Frame(len(scene["opacities"]), cam["width"], cam["height"], pair_capacity=fr_a.n_pairs + 70000)
+    fr.set_tuning(sort_mode=sort_mode.replace("_fused", ""), emit_fused=sort_mode.endswith("_fused"))
     fr.preprocess(R.scene_struct(sd), R.camera_struct(cam), "quadbox")
     fr.bin_emit(sync=False)
     fr.sort()
@@ -221,3 +251,17 @@ def test_invalid_arguments_rejected():
         fr.preprocess(R.scene_struct(sd), R.camera_struct(bad), "quadbox")
     with pytest.raises(N.QbError):
         fr.preprocess(R.scene_struct(sd), R.camera_struct(cam), 17)
+
+
+def test_tile_keys_accessor_is_bounded_by_its_output():
+    """qb_frame_tile_keys writes only the positions its output holds."""
+    import torch
+    from paper_2605_04844_gb300 import _native as N
+    scene, cam = c1_small(2000, 128, 128)
+    _, fr, A = run_forward(scene, cam, "quadbox")
+    buf = torch.full((16,), -7, dtype=torch.int32, device="cuda")
+    N.qb_frame_tile_keys(fr.frame, buf[:10])
+    torch.cuda.synchronize()
+    got = buf.cpu().numpy()
+    np.testing.assert_array_equal(got[:10], A["tile_keys"][:10])
+    assert (got[10:] == -7).all()
