@@ -382,7 +382,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), nullptr, frame_tileset(frame),
                                  zero_off, zero_off,
                                  at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
-                                 sort_hist_stride(), frame->sort_digit_bits, passes, frame->pair_capacity, s));
+                                 sort_hist_stride(), frame->sort_digit_bits, tile_bits, frame->pair_capacity, s));
         frame->reserved[1] = frame->sort_digit_bits;  // digit width the offsets were made for
     }
     frame->n_pairs = UINT64_MAX;
@@ -460,7 +460,8 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         if (fused && passes > 0 && a.mode != QB_BIN_QUADBOX_NAIVE) {
             const bool to_a = pass_writes_a(passes, 0);
             QB_CUDA(sort_clear(scratch, frame->pair_capacity, rb, 0, 1, s));
-            QB_CUDA(launch_emit_sweep(a, rb, passes > 1, to_a ? kA : kB, to_a ? vA : vB, sort_hist_table(scratch),
+            QB_CUDA(launch_emit_sweep(a, pass_geo(tile_bits, rb).bits[0], passes > 1, to_a ? kA : kB, to_a ? vA : vB,
+                                      sort_hist_table(scratch),
                                       sort_lookback(scratch, frame->pair_capacity, rb, 0), sort_counter(scratch, 0),
                                       s));
             frame->reserved[2] = 1;  // first pass left to qb_sort
@@ -514,12 +515,12 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
             QB_CUDA(launch_tile_count(src, n_max, n_dev, ntiles, counts, s));
             QB_CUDA(launch_tile_prep(nullptr, nullptr, counts, frame_tileset(frame), zero_off, zero_off,
                                      at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
-                                     sort_hist_stride(), rb, passes, frame->pair_capacity, s));
+                                     sort_hist_stride(), rb, tile_bits, frame->pair_capacity, s));
         }
         if (passes > 0)
             QB_CUDA(tile_sort_passes(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
                                      at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1), frame->pair_capacity,
-                                     n_max, n_dev, passes, frame->reserved[2], rb, at<void>(frame, L.sort_scratch),
+                                     n_max, n_dev, tile_bits, frame->reserved[2], rb, at<void>(frame, L.sort_scratch),
                                      err, s));
         frame->sorted_in_alt = 0;  // the values end in vals0; the tile of each is given by the ranges
         (void)ntiles;

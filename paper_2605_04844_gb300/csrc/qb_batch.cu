@@ -340,7 +340,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         uint2 *ranges = bat<uint2>(b, L.ranges) + v.tile0;
         QB_BCUDA(launch_tile_prep(diff, single, nullptr, v.ts, v.diff_off, v.single_off, ranges,
                                   sort_hist_table(bat<void>(b, L.sort)), sort_hist_stride(), t.sort_digit_bits,
-                                  tpasses, b->pair_capacity, s));
+                                  v.tile_bits, b->pair_capacity, s));
         // ---- QPass emit fused with the tile sort's first pass; the sorted
         // values end in this group's slot (buffer A = keysA + slot) ----
         uint32_t *slot = bat<uint32_t>(b, L.slots) + (size_t)gi * b->pair_capacity;
@@ -371,7 +371,8 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         if (tpasses > 0 && base_mode != QB_BIN_QUADBOX_NAIVE) {
             const bool to_a = pass_writes_a(tpasses, 0);
             QB_BCUDA(sort_clear(sort_scratch, b->pair_capacity, t.sort_digit_bits, 0, 1, s));
-            QB_BCUDA(launch_emit_sweep(e, t.sort_digit_bits, tpasses > 1, to_a ? keysA : keysB, to_a ? slot : valsT,
+            QB_BCUDA(launch_emit_sweep(e, pass_geo(v.tile_bits, t.sort_digit_bits).bits[0], tpasses > 1,
+                                       to_a ? keysA : keysB, to_a ? slot : valsT,
                                        sort_hist_table(sort_scratch),
                                        sort_lookback(sort_scratch, b->pair_capacity, t.sort_digit_bits, 0),
                                        sort_counter(sort_scratch, 0), s));
@@ -383,7 +384,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         }
         if (tpasses > first_pass)
             QB_BCUDA(tile_sort_passes(keysA, slot, keysB, valsT, b->pair_capacity, b->pair_capacity, npairs + gi,
-                                      tpasses, first_pass, t.sort_digit_bits, sort_scratch, err, s));
+                                      v.tile_bits, first_pass, t.sort_digit_bits, sort_scratch, err, s));
         // ---- persistent render over the group's tiles ----
         QB_BCUDA(cudaMemsetAsync(bat<uint32_t>(b, L.queue), 0, 4, s));
         RenderArgs r;

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_warp_kernel(EmitArgs a, 
 }
 
 // K3 fused with the first (lowest-digit) pass of the depth-first tile sort:
-// a block of 16 warps produces the 4096 pairs of one sort tile into shared
+// a block of kSortWarps warps produces the pairs of one sort tile into shared
 // memory (warp w the positions [256 w, 256 w + 256)), then runs the pass
 // body on them, so the pairs reach HBM once, already bucketed by their low
 // tile digit.  The bucket offsets of the pass come from the per-tile counts.
@@ -348,7 +348,7 @@ template <int RB, bool WRITE_KEYS>
 __global__ void __launch_bounds__(kSortBlock) emit_sweep_kernel(EmitArgs a, uint32_t *__restrict__ kout,
                                                                 uint32_t *__restrict__ vout,
                                                                 const uint32_t *__restrict__ bin_off,
-                                                                uint32_t *lookback, uint32_t *counter) {
+                                                                uint32_t *lookback, uint32_t *counter, uint32_t mask) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_k = reinterpret_cast<uint32_t *>(smem);
     uint32_t *s_v = s_k + kSortTile;
@@ -386,12 +386,13 @@ __global__ void __launch_bounds__(kSortBlock) emit_sweep_kernel(EmitArgs a, uint
         val[k] = valid ? wv[q] : 0u;
     }
     __syncthreads();  // the pass body reuses the staging memory
-    sweep_tile<RB, uint32_t, WRITE_KEYS>(key, val, P, tbase, tile, bin_off, lookback, 0, a.err, kout, vout, smem);
+    sweep_tile<RB, uint32_t, WRITE_KEYS>(key, val, (uint32_t)P, (uint32_t)tbase, tile, bin_off, lookback, 0, mask,
+                                         a.err, kout, vout, smem);
 }
 
 template <int RB, bool WRITE_KEYS>
 static cudaError_t launch_emit_sweep_b(const EmitArgs &a, uint32_t *kout, uint32_t *vout, const uint32_t *bin_off,
-                                       uint32_t *lookback, uint32_t *counter, cudaStream_t s) {
+                                       uint32_t *lookback, uint32_t *counter, uint32_t mask, cudaStream_t s) {
     static bool attrs = false;
     constexpr size_t smem = emit_sweep_smem<RB>();
     if (!attrs) {
@@ -404,7 +405,7 @@ static cudaError_t launch_emit_sweep_b(const EmitArgs &a, uint32_t *kout, uint32
     uint64_t blocks = (pairs + kSortTile - 1) / kSortTile;
     if (blocks == 0) blocks = 1;  // one block still flags an overflow
     note_launch(), emit_sweep_kernel<RB, WRITE_KEYS><<<(unsigned)blocks, kSortBlock, smem, s>>>(a, kout, vout, bin_off, lookback,
-                                                                               counter);
+                                                                               counter, mask);
     return cudaGetLastError();
 }
 
@@ -413,9 +414,14 @@ cudaError_t launch_emit_sweep(const EmitArgs &a, int digit_bits, bool write_keys
     if (a.n == 0) return cudaSuccess;
 #define QB_SWEEP_CASE(RB)                                                                                        \
     case RB:                                                                                                     \
-        return write_keys ? launch_emit_sweep_b<RB, true>(a, kout, vout, bin_off, lookback, counter, s)          \
-                          : launch_emit_sweep_b<RB, false>(a, kout, vout, bin_off, lookback, counter, s);
-    switch (digit_bits) {
+        return write_keys ? launch_emit_sweep_b<RB, true>(a, kout, vout, bin_off, lookback, counter, mask, s)    \
+                          : launch_emit_sweep_b<RB, false>(a, kout, vout, bin_off, lookback, counter, mask, s);
+    const uint32_t mask = (1u << digit_bits) - 1u;
+    switch (digit_bits < 4 ? 4 : digit_bits) {  // the width of the first pass (pass_geo)
+        QB_SWEEP_CASE(4)
+        QB_SWEEP_CASE(5)
+        QB_SWEEP_CASE(6)
+        QB_SWEEP_CASE(7)
         QB_SWEEP_CASE(8)
         QB_SWEEP_CASE(9)
         QB_SWEEP_CASE(10)
@@ -980,9 +986,9 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
 // exclusive bucket offsets of every pass of the tile sort.  One block.
 __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, const uint32_t *counts,
                                                          TileSet ts, TileOffsets off, uint2 *ranges, uint32_t *hist,
-                                                         int hist_stride, int rb, int passes, uint64_t capacity) {
-    extern __shared__ uint32_t sh_hist[];  // passes * 2^rb
-    const int R = 1 << rb;
+                                                         int hist_stride, int rb, PassGeo g, uint64_t capacity) {
+    extern __shared__ uint32_t sh_hist[];  // passes x 2^rb
+    const int R = 1 << rb, passes = g.passes;
     for (int j = threadIdx.x; j < passes * R; j += blockDim.x) sh_hist[j] = 0u;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int c = 0; c < (counts ? 0 : ts.n_cams); ++c) {
@@ -1044,13 +1050,15 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
         const uint32_t c = over ? 0u : count_of(t);
         ranges[t] = c ? make_uint2(run, run + c) : make_uint2(0u, 0u);  // [0,0) for an empty tile
         run += c;
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh_hist[p * R + ((t >> (p * rb)) & (R - 1))], c);
+        for (int p = 0; p < passes; ++p)
+            if (c) atomicAdd(&sh_hist[p * R + ((t >> g.shift[p]) & ((1 << g.bits[p]) - 1))], c);
     }
     __syncthreads();
     // exclusive offsets per pass
     for (int p = 0; p < passes; ++p) {
-        const int per_d = (R + blockDim.x - 1) / blockDim.x;
-        const int d0 = threadIdx.x * per_d, d1 = min(R, d0 + per_d);
+        const int Rp = 1 << g.bits[p];
+        const int per_d = (Rp + blockDim.x - 1) / blockDim.x;
+        const int d0 = threadIdx.x * per_d, d1 = min(Rp, d0 + per_d);
         uint32_t s = 0;
         for (int d = d0; d < d1; ++d) s += sh_hist[p * R + d];
         uint32_t tot;
@@ -1064,15 +1072,17 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
 
 cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint32_t *counts, const TileSet &ts,
                              const uint32_t *diff_off, const uint32_t *single_off, uint2 *ranges, uint32_t *hist,
-                             int hist_stride, int digit_bits, int passes, uint64_t capacity, cudaStream_t s) {
+                             int hist_stride, int digit_bits, int tile_bits, uint64_t capacity, cudaStream_t s) {
+    const PassGeo g = pass_geo(tile_bits, digit_bits);
+    const int passes = g.passes;
     TileOffsets off;
     for (int c = 0; c < kMaxGroupCams; ++c) {
         off.diff[c] = c < ts.n_cams ? diff_off[c] : 0u;
         off.single[c] = c < ts.n_cams ? single_off[c] : 0u;
     }
     const size_t smem = (size_t)passes * ((size_t)1 << digit_bits) * 4;
-    note_launch(), tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, counts, ts, off, ranges, hist, hist_stride, digit_bits,
-                                           passes, capacity);
+    note_launch(), tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, counts, ts, off, ranges, hist,
+                                                          hist_stride, digit_bits, g, capacity);
     return cudaGetLastError();
 }
 

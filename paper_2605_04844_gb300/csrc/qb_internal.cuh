@@ -59,6 +59,27 @@ void set_last_error(const char *msg);
 void note_launch();
 
 // ---- sort -------------------------------------------------------------------
+// Digit geometry of an LSD radix sort on bits [0, end_bit) with digits of at
+// most digit_bits: ceil(end_bit / digit_bits) passes whose widths differ by at
+// most one (13 bits at 8: 7 + 6), pass p on bits [shift[p], shift[p] + bits[p]).
+struct PassGeo {
+    int passes;
+    int shift[kMaxPasses], bits[kMaxPasses];
+};
+
+__host__ __device__ inline PassGeo pass_geo(int end_bit, int digit_bits) {
+    PassGeo g;
+    g.passes = end_bit > 0 ? (end_bit + digit_bits - 1) / digit_bits : 0;
+    int sh = 0;
+    for (int p = 0; p < kMaxPasses; ++p) {
+        const int w = p < g.passes ? end_bit / g.passes + (p < end_bit % g.passes ? 1 : 0) : 0;
+        g.shift[p] = sh;
+        g.bits[p] = w;
+        sh += w;
+    }
+    return g;
+}
+
 size_t sort_scratch_bytes(uint64_t n, int end_bit, int digit_bits);
 // Sorts pairs on bits [0, end_bit).  n_dev: device count (<= n_max) or null
 // when n_max is exact.  Returns the number of passes; result lies in the alt
@@ -82,11 +103,11 @@ uint32_t *sort_lookback(void *scratch, uint64_t n_cap, int digit_bits, int pass)
 uint32_t *sort_counter(void *scratch, int pass);
 cudaError_t sort_clear(void *scratch, uint64_t n_cap, int digit_bits, int first_pass, int end_pass,
                        cudaStream_t s);
-// Passes [first_pass, passes) of the tile sort: pass p writes buffer A when
-// passes - 1 - p is even, else B, reading the other; the last pass writes
-// values only (into A).
+// Passes [first_pass, passes) of the tile sort on bits [0, end_bit) (pass
+// widths from pass_geo): pass p writes buffer A when passes - 1 - p is even,
+// else B, reading the other; the last pass writes values only (into A).
 cudaError_t tile_sort_passes(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, uint64_t n_cap, uint64_t n_max,
-                             const uint64_t *n_dev, int passes, int first_pass, int digit_bits, void *scratch,
+                             const uint64_t *n_dev, int end_bit, int first_pass, int digit_bits, void *scratch,
                              uint32_t *err, cudaStream_t s);
 inline bool pass_writes_a(int passes, int p) { return ((passes - 1 - p) & 1) == 0; }
 

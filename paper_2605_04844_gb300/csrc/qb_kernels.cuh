@@ -180,7 +180,7 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
 // preprocess's difference arrays (counts null) or a count array.
 cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint32_t *counts, const TileSet &ts,
                              const uint32_t *diff_off, const uint32_t *single_off, uint2 *ranges, uint32_t *hist,
-                             int hist_stride, int digit_bits, int passes, uint64_t capacity, cudaStream_t s);
+                             int hist_stride, int digit_bits, int tile_bits, uint64_t capacity, cudaStream_t s);
 // Per-tile counts of n tile ids (counts zeroed here); ntiles <= kTileCountMax.
 constexpr int kTileCountMax = 24576;
 cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64_t *n_dev, int ntiles,

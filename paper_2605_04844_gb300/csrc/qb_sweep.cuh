@@ -2,9 +2,9 @@
 // (SortPairs, Sec. 2), shared by the plain pass kernel (qb_sort.cu) and the
 // QPass emit that performs the tile sort's first pass itself (qb_binning.cu).
 //
-// A block owns one tile of 4096 consecutive input positions; its keys arrive
+// A block owns one tile of kSortTile consecutive input positions; its keys arrive
 // in registers, warp-striped (item k of lane l of warp w is position
-// 256 w + 32 k + l of the tile).  The block counts its digits (shared
+// 32 kSortItems w + 32 k + l of the tile).  The block counts its digits (shared
 // atomics, order-free), publishes the counts and looks back over earlier
 // tiles for their running totals, ranks its keys per warp in input order,
 // and scatters keys then values through shared memory so that runs of equal
@@ -84,29 +84,28 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *to
     return incl - v + before;
 }
 
-// Shared memory of one pass: the scatter buffer (keys, then values), per-warp
-// digit counters, and per-digit global base, local start and tile count.
+// Shared memory of one pass: the scatter buffer ((key, value) pairs for 32-bit
+// keys; keys, then values, for 64-bit keys), per-warp digit counters, and
+// per-digit global base, local start and tile count.
 template <int RB, typename KeyT>
 constexpr size_t sweep_smem() {
-    return (size_t)kSortTile * sizeof(KeyT) + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)3 * (1 << RB) * 4;
+    return (size_t)kSortTile * 8 + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)3 * (1 << RB) * 4;
 }
 
-// One pass over the tile `tile` (positions [tbase, tbase + 4096) of n).
-// bin_off: the pass's exclusive bucket offsets; lookback: the pass's status
-// words [tiles][2^RB].  With WRITE_KEYS false only the values are written
-// (the last pass, whose keys are implied by the per-tile ranges).
+// One pass over the tile `tile` (positions [tbase, tbase + kSortTile) of n) on the
+// digit (key >> shift) & mask, mask < 2^RB.  bin_off: the pass's exclusive
+// bucket offsets; lookback: the pass's status words [tiles][2^RB].  With
+// WRITE_KEYS false only the values are written (the last pass, whose keys are
+// implied by the per-tile ranges).
 template <int RB, typename KeyT, bool WRITE_KEYS>
 __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const uint32_t (&val)[kSortItems],
-                                           uint64_t n, uint64_t tbase, uint32_t tile,
+                                           uint32_t n, uint32_t tbase, uint32_t tile,
                                            const uint32_t *__restrict__ bin_off, uint32_t *lookback, int shift,
-                                           uint32_t *err, KeyT *__restrict__ kout, uint32_t *__restrict__ vout,
-                                           uint8_t *smem) {
+                                           uint32_t mask, uint32_t *err, KeyT *__restrict__ kout,
+                                           uint32_t *__restrict__ vout, uint8_t *smem) {
     constexpr int R = 1 << RB;
-    constexpr uint32_t MASK = R - 1;
     constexpr int PER = (R + kSortBlock - 1) / kSortBlock;
-    KeyT *s_keys = reinterpret_cast<KeyT *>(smem);
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem);
-    uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem + (size_t)kSortTile * sizeof(KeyT));
+    uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem + (size_t)kSortTile * 8);
     uint32_t *s_gbase = reinterpret_cast<uint32_t *>(s_whist + kSortWarps * R);
     uint32_t *s_lstart = s_gbase + R;
     uint32_t *s_bcount = s_lstart + R;
@@ -115,22 +114,24 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
     for (int j = tid; j < kSortWarps * R / 2; j += kSortBlock) reinterpret_cast<uint32_t *>(s_whist)[j] = 0u;
     for (int j = tid; j < R; j += kSortBlock) s_bcount[j] = 0u;
     __syncthreads();
-    const uint64_t wbase = tbase + (uint64_t)wid * (32 * kSortItems);
-    uint32_t rank[kSortItems];
+    const uint32_t wbase = tbase + (uint32_t)wid * (32 * kSortItems);
+    // items of this warp that exist: item k of lane l is valid when 32 k + l < wcount
+    const int wcount = n > wbase ? (int)min(n - wbase, (uint32_t)(32 * kSortItems)) : 0;
+    uint32_t dig[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) dig[k] = (uint32_t)(key[k] >> shift) & mask;
 
     // ---- early digit counts of the tile ----
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k)
-        if (wbase + 32 * k + lane < n) atomicAdd(&s_bcount[(uint32_t)(key[k] >> shift) & MASK], 1u);
+        if (32 * k + lane < wcount) atomicAdd(&s_bcount[dig[k]], 1u);
     __syncthreads();
 
-    // ---- publish, look back, publish the inclusive prefix ----
+    // ---- publish this tile's counts, prefetch the look-back ----
     // One status word per (tile, digit): a 2-bit flag (aggregate = the tile's
     // own count, inclusive = running total through the tile) and a 30-bit
-    // count.  Each thread walks back for its digits, kLookWindow words at a
-    // time (their addresses do not depend on what is read), adding aggregates
-    // until it meets an inclusive total; when the next word is not yet
-    // published it polls that word alone, sleeping between polls.
+    // count.  The first look-back window is loaded here and consumed after the
+    // ranking, so its latency overlaps the warps' ranking work.
     uint32_t cnt[PER], tsum = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
@@ -139,11 +140,46 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
         tsum += cnt[j];
     }
     uint32_t *lb = lookback + (size_t)tile * R;
+    uint32_t pre_sv[kLookWindow];  // for this thread's first digit
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         int d = tid * PER + j;
         if (d < R) st_relaxed(lb + d, (tile == 0 ? kFlagIncl : kFlagAgg) | cnt[j]);
     }
+#pragma unroll
+    for (int w = 0; w < kLookWindow; ++w)
+        pre_sv[w] = (tid * PER < R && (int64_t)tile - 1 - w >= 0)
+                        ? ld_relaxed(lookback + (size_t)(tile - 1 - w) * R + tid * PER)
+                        : kFlagIncl;
+
+    // ---- rank within the warp, in original order ----
+    // Lanes holding the same digit are found with one ballot per digit bit;
+    // invalid lanes carry the digit R (bit RB), which keeps them apart.
+    uint16_t *wh = s_whist + wid * R;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const bool valid = 32 * k + lane < wcount;
+        const uint32_t d = valid ? dig[k] : (uint32_t)R;
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b <= RB; ++b) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+        const uint32_t pre = valid ? (uint32_t)wh[d] : 0u;
+        const uint32_t lower = __popc(peers & lt);
+        __syncwarp();
+        if (valid && lower == 0) wh[d] = (uint16_t)(pre + __popc(peers));
+        __syncwarp();
+        rank[k] = pre + lower;
+    }
+
+    // ---- look back for the running totals, publish the inclusive prefix ----
+    // Each thread walks back for its digits, kLookWindow words at a time
+    // (their addresses do not depend on what is read), adding aggregates until
+    // it meets an inclusive total; when the next word is not yet published it
+    // polls that word alone, sleeping between polls.
     uint32_t btotal;
     uint32_t run = block_excl_scan_u32(tsum, &btotal);  // contains __syncthreads
 #pragma unroll
@@ -157,11 +193,14 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
             int64_t t = (int64_t)tile - 1;
             int spins = 0;
             bool done = false;
+            bool first = j == 0;
             while (!done && t >= 0) {
                 uint32_t sv[kLookWindow];
 #pragma unroll
                 for (int w = 0; w < kLookWindow; ++w)
-                    sv[w] = (t - w >= 0) ? ld_relaxed(lookback + (size_t)(t - w) * R + d) : kFlagIncl;
+                    sv[w] = first ? pre_sv[w]
+                                  : ((t - w >= 0) ? ld_relaxed(lookback + (size_t)(t - w) * R + d) : kFlagIncl);
+                first = false;
                 int used = 0;
 #pragma unroll
                 for (int w = 0; w < kLookWindow; ++w) {
@@ -193,30 +232,6 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
     }
     __syncthreads();
 
-    // ---- rank within the warp, in original order ----
-    // Lanes holding the same digit are found with one ballot per digit bit.
-    uint16_t *wh = s_whist + wid * R;
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const bool valid = wbase + 32 * k + lane < n;
-        const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & MASK : (uint32_t)R;
-        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        uint32_t peers = valid ? vmask : ~vmask;
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bb : ~bb;
-        }
-        const uint32_t pre = valid ? (uint32_t)wh[d] : 0u;
-        const uint32_t lower = __popc(peers & lt);
-        __syncwarp();
-        if (valid && lower == 0) wh[d] = (uint16_t)(pre + __popc(peers));
-        __syncwarp();
-        rank[k] = pre + lower;
-    }
-    __syncthreads();
-
     // ---- per digit: exclusive prefix over the warps ----
     for (int d = tid; d < R; d += kSortBlock) {
         uint32_t r = 0;
@@ -229,39 +244,67 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
     }
     __syncthreads();
 
-    // ---- keys: scatter to block order in shared memory, then out ----
+    const uint32_t tcount = min(n - tbase, (uint32_t)kSortTile);
+    if constexpr (sizeof(KeyT) == 4) {
+        // ---- (key, value) pairs to block order in shared memory, then out ----
+        uint2 *s_pairs = reinterpret_cast<uint2 *>(smem);
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        if (wbase + 32 * k + lane < n) {
-            uint32_t d = (uint32_t)(key[k] >> shift) & MASK;
-            uint32_t lr = s_lstart[d] + s_whist[wid * R + d] + rank[k];
-            s_keys[lr] = key[k];
-            rank[k] = lr;
+        for (int k = 0; k < kSortItems; ++k) {
+            if (32 * k + lane < wcount) {
+                const uint32_t d = dig[k];
+                s_pairs[s_lstart[d] + s_whist[wid * R + d] + rank[k]] = make_uint2((uint32_t)key[k], val[k]);
+            }
         }
-    }
-    __syncthreads();
-    const uint32_t tcount = (uint32_t)min((uint64_t)kSortTile, n - tbase);
-    uint32_t dest[kSortItems];
+        __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        uint32_t j = tid + k * kSortBlock;
-        if (j < tcount) {
-            const KeyT kk = s_keys[j];
-            uint32_t d = (uint32_t)(kk >> shift) & MASK;
-            dest[k] = s_gbase[d] + (j - s_lstart[d]);
-            if (WRITE_KEYS && dest[k] < n) kout[dest[k]] = kk;  // dest >= n only after a look-back timeout
+        for (int k = 0; k < kSortItems; ++k) {
+            const uint32_t j = tid + k * kSortBlock;
+            if (j < tcount) {
+                const uint2 kv = s_pairs[j];
+                const uint32_t d = (kv.x >> shift) & mask;
+                const uint32_t dest = s_gbase[d] + (j - s_lstart[d]);
+                if (dest < n) {  // dest >= n only after a look-back timeout
+                    if (WRITE_KEYS) kout[dest] = (KeyT)kv.x;
+                    vout[dest] = kv.y;
+                }
+            }
         }
-    }
-    __syncthreads();
-    // ---- values through the same permutation ----
+    } else {
+        // ---- keys: scatter to block order in shared memory, then out ----
+        KeyT *s_keys = reinterpret_cast<KeyT *>(smem);
+        uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem);
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k)
-        if (wbase + 32 * k + lane < n) s_vals[rank[k]] = val[k];
-    __syncthreads();
+        for (int k = 0; k < kSortItems; ++k) {
+            if (32 * k + lane < wcount) {
+                const uint32_t d = dig[k];
+                const uint32_t lr = s_lstart[d] + s_whist[wid * R + d] + rank[k];
+                s_keys[lr] = key[k];
+                rank[k] = lr;
+            }
+        }
+        __syncthreads();
+        uint32_t dest[kSortItems];
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        uint32_t j = tid + k * kSortBlock;
-        if (j < tcount && dest[k] < n) vout[dest[k]] = s_vals[j];
+        for (int k = 0; k < kSortItems; ++k) {
+            const uint32_t j = tid + k * kSortBlock;
+            if (j < tcount) {
+                const KeyT kk = s_keys[j];
+                const uint32_t d = (uint32_t)(kk >> shift) & mask;
+                dest[k] = s_gbase[d] + (j - s_lstart[d]);
+                if (WRITE_KEYS && dest[k] < n) kout[dest[k]] = kk;
+            }
+        }
+        __syncthreads();
+        // ---- values through the same permutation ----
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k)
+            if (32 * k + lane < wcount) s_vals[rank[k]] = val[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            const uint32_t j = tid + k * kSortBlock;
+            if (j < tcount && dest[k] < n) vout[dest[k]] = s_vals[j];
+        }
     }
 }
 
