@@ -597,6 +597,7 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
     b.g_screen = gscreen;
     QB_CUDA(launch_render_bwd(b, s));
     PreBwdArgs p;
+    std::memset(&p, 0, sizeof(p));
     p.n = scene->n;
     p.means = scene->means;
     p.scales = scene->scales;
@@ -612,6 +613,8 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
     p.gq = grads->quats;
     p.go = grads->opacities;
     p.gsh = grads->sh;
+    p.sh_vec4 = reinterpret_cast<uintptr_t>(scene->sh) % 16 == 0;
+    p.gsh_vec4 = reinterpret_cast<uintptr_t>(grads->sh) % 16 == 0;
     QB_CUDA(launch_preprocess_bwd(p, scene->sh_degree, s));
     return QB_OK;
 }

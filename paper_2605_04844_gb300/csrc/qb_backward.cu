@@ -2,9 +2,9 @@
 // differentiable rasteriser (Sec. 4.1 states the rasteriser is differentiable;
 // the gradients below differentiate Eq. 2 and the Sec. 2 projection).
 //
-// K7: a 256-thread block per tile (one pixel per thread) walks the tile list
-// in reverse, from the largest last-contributor position of its pixels down
-// to 0.  Each pixel recomputes alpha exactly as the forward did and the
+// K7: a 128-thread block per tile (two pixels of a column per thread) walks
+// the tile list in reverse, from the largest last-contributor position of its
+// pixels down to 0.  Each pixel recomputes alpha exactly as the forward did and the
 // transmittance by division, T_k = T_{k+1} / (1 - alpha_k), keeping the colour
 // behind the current entry, B_k = sum_{i>k} T_i alpha_i c_i + T_final bg:
 //   dC/dc_k     = T_k alpha_k
@@ -25,7 +25,8 @@
 
 namespace qb {
 
-constexpr int kBwdThreads = kTile * kTile;
+constexpr int kBwdThreads = kTile * kTile / 2;  // two pixels per thread
+constexpr int kBwdBatch = 256;                  // entries staged per shared-memory batch
 
 // float -> double by rebuilding the IEEE-754 bit pattern with integer
 // operations (exponent rebias 127 -> 1023, mantissa 23 -> 52 bits), so the
@@ -77,6 +78,51 @@ __device__ __forceinline__ void warp_reduce9_add(const float g[9], double *dst, 
     if (!(lane & 1) && ix < 3 && iw < 5 && iv < 9 && z != 0.f) atomicAdd(dst + iv, widen(z));
 }
 
+// One pixel's part of the gradient of entry (m, c, rgb) at column offset dx
+// (the column terms A, Bt shared with the thread's other pixel), added to gv.
+struct BwdPix {
+    float T, B0, B1, B2, g0, g1, g2;
+    int last;
+};
+
+__device__ __forceinline__ void bwd_pixel(BwdPix &q, int p, float4 m, float4 c, float4 rgb, float dx, float A, float Bt,
+                                          float pyf, float gv[9], bool &contrib) {
+    if (p >= q.last) return;
+    const float dy = m.y - pyf;
+    const float power = power_from(A, Bt, c.z, dy);
+    if (!(power <= 0.f && power >= m.z)) return;
+    const float G = __expf(power);
+    const float oG = __fmul_rn(m.w, G);
+    const float alpha = fminf(kAlphaMax, oG);
+    if (alpha < kAlphaMin) return;
+    contrib = true;
+    const float inv = __frcp_rn(1.f - alpha);
+    q.T = q.T * inv;  // transmittance in front of this entry
+    const float w = alpha * q.T;
+    gv[6] = fmaf(w, q.g0, gv[6]);
+    gv[7] = fmaf(w, q.g1, gv[7]);
+    gv[8] = fmaf(w, q.g2, gv[8]);
+    const float dalpha = q.g0 * (q.T * rgb.x - q.B0 * inv) + q.g1 * (q.T * rgb.y - q.B1 * inv) +
+                         q.g2 * (q.T * rgb.z - q.B2 * inv);
+    q.B0 = fmaf(w, rgb.x, q.B0);
+    q.B1 = fmaf(w, rgb.y, q.B1);
+    q.B2 = fmaf(w, rgb.z, q.B2);
+    if (oG < kAlphaMax) {
+        // power = -d^T Lambda d / 2 with Lambda = Sigma^-1 and u = Lambda d:
+        // dpower/dmu = -u, dpower/dSigma = u u^T / 2
+        const float dpower = dalpha * oG;
+        const float ux = -2.f * c.x * dx - c.y * dy, uy = -c.y * dx - 2.f * c.z * dy;
+        gv[5] = fmaf(G, dalpha, gv[5]);
+        gv[0] = fmaf(-dpower, ux, gv[0]);
+        gv[1] = fmaf(-dpower, uy, gv[1]);
+        gv[2] = fmaf(0.5f * dpower * ux, ux, gv[2]);
+        gv[3] = fmaf(dpower * ux, uy, gv[3]);
+        gv[4] = fmaf(0.5f * dpower * uy, uy, gv[4]);
+    }
+}
+
+// A tile by kBwdThreads threads, each owning two pixels of one column (rows r
+// and r + 8), like the forward.
 __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile, int ci, uint32_t *s_id, float4 *s_m,
                                                 float4 *s_c, float4 *s_rgb, int *s_maxlast) {
     const CamTile &C = a.ts.cam[ci];
@@ -84,86 +130,63 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
     const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31;
     const int px = tx * kTile + (tid & (kTile - 1));
-    const int py = ty * kTile + (tid >> kTileShift);
-    const bool inside = px < C.W && py < C.H;
-    const float pxf = (float)px, pyf = (float)py;
-    const size_t pix = (size_t)py * C.W + px, plane = (size_t)C.W * C.H;
+    const int py0 = ty * kTile + (tid >> kTileShift), py1 = py0 + 8;
+    const float pxf = (float)px, py0f = (float)py0, py1f = (float)py1;
+    const size_t plane = (size_t)C.W * C.H;
+    const float *dl = a.dL_dimg + 3 * C.pix_base;
 
-    float T = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    int last = 0;
-    if (inside) {
-        const float *dl = a.dL_dimg + 3 * C.pix_base;
-        T = a.tfinal[C.pix_base + pix];
-        last = a.ncontrib[C.pix_base + pix];
-        g0 = dl[pix];
-        g1 = dl[plane + pix];
-        g2 = dl[2 * plane + pix];
+    BwdPix q[2];
+    const int pys[2] = {py0, py1};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        q[h] = BwdPix{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        if (px < C.W && pys[h] < C.H) {
+            const size_t pix = (size_t)pys[h] * C.W + px;
+            q[h].T = a.tfinal[C.pix_base + pix];
+            q[h].last = a.ncontrib[C.pix_base + pix];
+            q[h].g0 = dl[pix];
+            q[h].g1 = dl[plane + pix];
+            q[h].g2 = dl[2 * plane + pix];
+        }
+        q[h].B0 = q[h].T * a.bg[0];
+        q[h].B1 = q[h].T * a.bg[1];
+        q[h].B2 = q[h].T * a.bg[2];
     }
-    float B0 = T * a.bg[0], B1 = T * a.bg[1], B2 = T * a.bg[2];
     if (tid == 0) *s_maxlast = 0;
     __syncthreads();
-    if (last > 0) atomicMax(s_maxlast, last);
+    const int mylast = max(q[0].last, q[1].last);
+    if (mylast > 0) atomicMax(s_maxlast, mylast);
     __syncthreads();
     const int maxlast = *s_maxlast;
     const uint32_t rstart = a.ranges[gtile].x;
 
-    for (int end = maxlast; end > 0; end -= kBwdThreads) {
-        const int cnt = min(kBwdThreads, end);
+    for (int end = maxlast; end > 0; end -= kBwdBatch) {
+        const int cnt = min(kBwdBatch, end);
         const int start = end - cnt;
         __syncthreads();
-        if (tid < cnt) {
-            const uint32_t g = a.vals[rstart + start + tid];
-            s_id[tid] = g;
+        for (int k = tid; k < cnt; k += kBwdThreads) {
+            const uint32_t g = a.vals[rstart + start + k];
+            s_id[k] = g;
             const float2 m = a.xy[g];
             const float4 co = a.conic_o[g];
-            s_m[tid] = make_float4(m.x, m.y, skip_threshold(co.w), co.w);
-            s_c[tid] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, 0.f);
-            s_rgb[tid] = a.rgbd[g];
+            s_m[k] = make_float4(m.x, m.y, skip_threshold(co.w), co.w);
+            s_c[k] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, 0.f);
+            s_rgb[k] = a.rgbd[g];
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int p = start + j;
             float gv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
-            if (p < last) {
+            if (p < mylast) {
                 const float4 m = s_m[j];
                 const float4 c = s_c[j];
-                const float dx = m.x - pxf, dy = m.y - pyf;
+                const float4 rgb = s_rgb[j];
+                const float dx = m.x - pxf;
                 float A, Bt;
                 power_terms(c.x, c.y, dx, A, Bt);
-                const float power = power_from(A, Bt, c.z, dy);
-                if (power <= 0.f && power >= m.z) {
-                    const float G = __expf(power);
-                    const float oG = __fmul_rn(m.w, G);
-                    const float alpha = fminf(kAlphaMax, oG);
-                    if (alpha >= kAlphaMin) {
-                        contrib = true;
-                        const float inv = __frcp_rn(1.f - alpha);
-                        T = T * inv;  // transmittance in front of this entry
-                        const float4 rgb = s_rgb[j];
-                        const float w = alpha * T;
-                        gv[6] = w * g0;
-                        gv[7] = w * g1;
-                        gv[8] = w * g2;
-                        const float dalpha = g0 * (T * rgb.x - B0 * inv) + g1 * (T * rgb.y - B1 * inv) +
-                                             g2 * (T * rgb.z - B2 * inv);
-                        B0 = fmaf(w, rgb.x, B0);
-                        B1 = fmaf(w, rgb.y, B1);
-                        B2 = fmaf(w, rgb.z, B2);
-                        if (oG < kAlphaMax) {
-                            // power = -d^T Lambda d / 2 with Lambda = Sigma^-1 and u = Lambda d:
-                            // dpower/dmu = -u, dpower/dSigma = u u^T / 2
-                            const float dpower = dalpha * oG;
-                            const float ux = -2.f * c.x * dx - c.y * dy, uy = -c.y * dx - 2.f * c.z * dy;
-                            gv[5] = G * dalpha;
-                            gv[0] = -dpower * ux;
-                            gv[1] = -dpower * uy;
-                            gv[2] = 0.5f * dpower * ux * ux;
-                            gv[3] = dpower * ux * uy;
-                            gv[4] = 0.5f * dpower * uy * uy;
-                        }
-                    }
-                }
+                bwd_pixel(q[0], p, m, c, rgb, dx, A, Bt, py0f, gv, contrib);
+                bwd_pixel(q[1], p, m, c, rgb, dx, A, Bt, py1f, gv, contrib);
             }
             if (__ballot_sync(0xffffffffu, contrib)) warp_reduce9_add(gv, a.g_screen + (size_t)s_id[j] * 9, lane);
         }
@@ -171,15 +194,15 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
 }
 
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
-    __shared__ uint32_t s_id[kBwdThreads];
-    __shared__ float4 s_m[kBwdThreads], s_c[kBwdThreads], s_rgb[kBwdThreads];
+    __shared__ uint32_t s_id[kBwdBatch];
+    __shared__ float4 s_m[kBwdBatch], s_c[kBwdBatch], s_rgb[kBwdBatch];
     __shared__ int s_maxlast;
     render_bwd_tile(a, blockIdx.x, 0, s_id, s_m, s_c, s_rgb, &s_maxlast);
 }
 
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent_kernel(BwdArgs a) {
-    __shared__ uint32_t s_id[kBwdThreads];
-    __shared__ float4 s_m[kBwdThreads], s_c[kBwdThreads], s_rgb[kBwdThreads];
+    __shared__ uint32_t s_id[kBwdBatch];
+    __shared__ float4 s_m[kBwdBatch], s_c[kBwdBatch], s_rgb[kBwdBatch];
     __shared__ int s_maxlast;
     __shared__ uint32_t s_next;
     for (;;) {
@@ -209,21 +232,68 @@ cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int DEG>
+// SH rows of 3 K floats, as float4 when K is even and the row pointer 16-byte
+// aligned (all rows then are).
+template <int K>
+__device__ __forceinline__ void load_row(const float *p, bool vec, float (&out)[K * 3]) {
+    if constexpr ((K * 3) % 4 == 0) {
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < (K * 3) / 4; ++q) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + q);
+                out[4 * q] = v.x;
+                out[4 * q + 1] = v.y;
+                out[4 * q + 2] = v.z;
+                out[4 * q + 3] = v.w;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K * 3; ++k) out[k] = __ldg(p + k);
+}
+
+// grad += Y[k] * gcol[c] at row position 3 k + c.
+template <int K>
+__device__ __forceinline__ void add_row(float *p, bool vec, const float (&Y)[16], const float (&gcol)[3]) {
+    if constexpr ((K * 3) % 4 == 0) {
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < (K * 3) / 4; ++q) {
+                float4 v = reinterpret_cast<float4 *>(p)[q];
+                v.x += Y[(4 * q) / 3] * gcol[(4 * q) % 3];
+                v.y += Y[(4 * q + 1) / 3] * gcol[(4 * q + 1) % 3];
+                v.z += Y[(4 * q + 2) / 3] * gcol[(4 * q + 2) % 3];
+                v.w += Y[(4 * q + 3) / 3] * gcol[(4 * q + 3) % 3];
+                reinterpret_cast<float4 *>(p)[q] = v;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K * 3; ++k) p[k] += Y[k / 3] * gcol[k % 3];
+}
+
+// SINGLE: one camera (a frame); the SH gradient Y gcol^T is then written
+// directly instead of being summed over cameras in registers.
+template <int DEG, bool SINGLE>
 __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PreBwdArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int KS = SINGLE ? 1 : K;  // sizes of the multi-camera accumulator
     const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
     const float sc0 = a.scales[3 * i], sc1 = a.scales[3 * i + 1], sc2 = a.scales[3 * i + 2];
     const float qw = a.quats[4 * i], qx = a.quats[4 * i + 1], qy = a.quats[4 * i + 2], qz = a.quats[4 * i + 3];
     const float *sh = a.sh + (size_t)i * K * 3;
+    const bool vec = a.sh_vec4;
     float gmean[3] = {0.f, 0.f, 0.f}, gsc[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
-    float gsh[K * 3];
+    float gsh[KS * 3];
 #pragma unroll
-    for (int k = 0; k < K * 3; ++k) gsh[k] = 0.f;
+    for (int k = 0; k < KS * 3; ++k) gsh[k] = 0.f;
+    float Y1[16], gcol1[3] = {0.f, 0.f, 0.f};  // SINGLE: the one camera's basis and colour gradient
     bool any = false;
-    for (int cam = 0; cam < a.cams.n_cams; ++cam) {
+    for (int cam = 0; cam < (SINGLE ? 1 : a.cams.n_cams); ++cam) {
         const size_t rec = (size_t)cam * a.n + i;
         const int meta = a.meta[rec];
         if (!(meta & kMetaVisible)) continue;
@@ -322,15 +392,24 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PreBwdArgs a) {
         float gcol[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) gcol[ch] = (meta >> (kMetaClampShift + ch)) & 1 ? 0.f : grgb[ch];
-        float wsh[16];
+        if constexpr (SINGLE) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            gsh[3 * k] += Y[k] * gcol[0];
-            gsh[3 * k + 1] += Y[k] * gcol[1];
-            gsh[3 * k + 2] += Y[k] * gcol[2];
-            wsh[k] = sh[3 * k] * gcol[0] + sh[3 * k + 1] * gcol[1] + sh[3 * k + 2] * gcol[2];
+            for (int k = 0; k < 16; ++k) Y1[k] = k < K ? Y[k] : 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) gcol1[ch] = gcol[ch];
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                gsh[3 * k] += Y[k] * gcol[0];
+                gsh[3 * k + 1] += Y[k] * gcol[1];
+                gsh[3 * k + 2] += Y[k] * gcol[2];
+            }
         }
         if (DEG > 0) {
+            float c[K * 3], wsh[16];
+            load_row<K>(sh, vec, c);
+#pragma unroll
+            for (int k = 0; k < K; ++k) wsh[k] = c[3 * k] * gcol[0] + c[3 * k + 1] * gcol[1] + c[3 * k + 2] * gcol[2];
             float ddx, ddy, ddz;
             sh_grad<DEG>(dx, dy, dz, wsh, ddx, ddy, ddz);
             const float r = ddx * dx + ddy * dy + ddz * dz;
@@ -352,18 +431,27 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(PreBwdArgs a) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) a.gq[4 * i + j] += gq[j];
     float *gshp = a.gsh + (size_t)i * K * 3;
+    if constexpr (SINGLE) {
+        add_row<K>(gshp, a.gsh_vec4, Y1, gcol1);
+    } else {
 #pragma unroll
-    for (int k = 0; k < K * 3; ++k) gshp[k] += gsh[k];
+        for (int k = 0; k < K * 3; ++k) gshp[k] += gsh[k];
+    }
 }
 
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     dim3 grid((a.n + 255) / 256), block(256);
+    const bool one = a.cams.n_cams == 1;
     switch (deg) {
-    case 0: note_launch(), preprocess_bwd_kernel<0><<<grid, block, 0, s>>>(a); break;
-    case 1: note_launch(), preprocess_bwd_kernel<1><<<grid, block, 0, s>>>(a); break;
-    case 2: note_launch(), preprocess_bwd_kernel<2><<<grid, block, 0, s>>>(a); break;
-    default: note_launch(), preprocess_bwd_kernel<3><<<grid, block, 0, s>>>(a); break;
+    case 0: one ? (note_launch(), preprocess_bwd_kernel<0, true><<<grid, block, 0, s>>>(a))
+                : (note_launch(), preprocess_bwd_kernel<0, false><<<grid, block, 0, s>>>(a)); break;
+    case 1: one ? (note_launch(), preprocess_bwd_kernel<1, true><<<grid, block, 0, s>>>(a))
+                : (note_launch(), preprocess_bwd_kernel<1, false><<<grid, block, 0, s>>>(a)); break;
+    case 2: one ? (note_launch(), preprocess_bwd_kernel<2, true><<<grid, block, 0, s>>>(a))
+                : (note_launch(), preprocess_bwd_kernel<2, false><<<grid, block, 0, s>>>(a)); break;
+    default: one ? (note_launch(), preprocess_bwd_kernel<3, true><<<grid, block, 0, s>>>(a))
+                 : (note_launch(), preprocess_bwd_kernel<3, false><<<grid, block, 0, s>>>(a)); break;
     }
     return cudaGetLastError();
 }

@@ -468,6 +468,8 @@ qb_status qb_render_batch_bwd(qb_batch *b, const qb_scene *scene, const qb_camer
         p.gq = grads->quats;
         p.go = grads->opacities;
         p.gsh = grads->sh;
+        p.sh_vec4 = reinterpret_cast<uintptr_t>(scene->sh) % 16 == 0;
+        p.gsh_vec4 = reinterpret_cast<uintptr_t>(grads->sh) % 16 == 0;
         QB_BCUDA(launch_preprocess_bwd(p, scene->sh_degree, s));
     }
     return QB_OK;

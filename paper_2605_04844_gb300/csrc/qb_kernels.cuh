@@ -154,6 +154,7 @@ struct PreBwdArgs {
     const int *meta;          // [n_cams * n]
     const double *g_screen;   // [n_cams * n][9]
     float *gm, *gs, *gq, *go, *gsh;
+    bool sh_vec4, gsh_vec4;   // sh / gsh rows may be accessed as float4 (16-byte aligned)
 };
 
 cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s);
