@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--sort-mode", default="depth_first", choices=["depth_first", "full_key", "chunked"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched comparison")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 3M-Gaussian zoom sweep")
+    ap.add_argument("--no-c4", action="store_true", help="skip the 500k forward+backward (L1 loss) case")
     ap.add_argument("--batch-cams", type=int, default=64)
     ap.add_argument("--batch-n", type=int, default=1_000_000)
     ap.add_argument("--out", default=None, help="also write the JSON line here")
@@ -158,37 +160,69 @@ def run_ours(args, rank, world, local_rank):
 
     STAGES = ("preprocess", "emit", "sort", "render", "backward")
 
+    # per-kernel timeline: the library calls the hook just before each launch;
+    # an event recorded there on the launching stream ends the previous kernel
+    timeline = [None]
+    ext_streams = {}
+
+    def on_launch(name, handle):
+        if timeline[0] is None:
+            return
+        st = stream if handle in (0, stream.cuda_stream) else ext_streams.setdefault(
+            handle, torch.cuda.ExternalStream(handle))
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(st)
+        timeline[0].append((name, e))
+
+    N.qb_set_launch_hook(on_launch)
+
+    def mark(e):
+        e.record(stream)
+        if timeline[0] is not None:
+            timeline[0].append(("", e))
+
     def step(fr, with_bwd, ev):
-        ev[0].record(stream)
+        mark(ev[0])
         fr.preprocess(scene_s, cam_s, mode_of[id(fr)])
-        ev[1].record(stream)
+        mark(ev[1])
         fr.bin_emit(sync=False)
-        ev[2].record(stream)
+        mark(ev[2])
         fr.sort()
-        ev[3].record(stream)
+        mark(ev[3])
         fr.render(bg, img)
-        ev[4].record(stream)
+        mark(ev[4])
         if with_bwd:
             for g in grads.values():
                 g.zero_()
             N.qb_render_bwd(fr.frame, scene_s, cam_s, bg, dL, gs, None)
-            ev[5].record(stream)
+            mark(ev[5])
 
     mode_of = {id(fr): ("aabb3s" if name == "aabb3s" else "quadbox") for name, fr in frames.items()}
 
-    def run_phase(mode, with_bwd, steps, warmup):
+    def run_phase(mode, with_bwd, steps, warmup, kernels=None):
+        """Times `steps` steps; with a dict `kernels`, also every kernel of the
+        library launched in them (per name: launches and ms per step, ms per
+        launch), from the events recorded at each launch."""
         fr = frames[mode]
         nev = 6 if with_bwd else 5
         for _ in range(warmup):
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(nev)]
             step(fr, with_bwd, evs)
         torch.cuda.synchronize()
-        recs = []
+        recs, lines = [], []
         for _ in range(steps):
             flush.zero_()  # L2 flush between timed steps (outside the events)
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(nev)]
             l0 = N.qb_kernel_launches()
+            if kernels is not None:
+                # the GPU spins while the host queues the step and its per-launch
+                # events, so the kernels then run back to back between them
+                torch.cuda._sleep(KERNEL_TIMING_SPIN_CYCLES)
+                timeline[0] = []
             step(fr, with_bwd, evs)
+            if kernels is not None:
+                lines.append(timeline[0])
+                timeline[0] = None
             launches[0] += N.qb_kernel_launches() - l0
             recs.append(evs)
         torch.cuda.synchronize()
@@ -200,6 +234,18 @@ def run_ours(args, rank, world, local_rank):
                 dt = evs[i].elapsed_time(evs[i + 1])
                 per_stage[STAGES[i]] += dt
                 total += dt
+        if kernels is not None:
+            for tl in lines:
+                for i, (name, e) in enumerate(tl):
+                    if name and i + 1 < len(tl):
+                        k = kernels.setdefault(name, {"launches": 0, "ms": 0.0})
+                        k["launches"] += 1
+                        k["ms"] += e.elapsed_time(tl[i + 1][1])
+            for k in kernels.values():
+                k["ms_per_launch"] = round(k["ms"] / max(1, k["launches"]), 4)
+                k["launches_per_step"] = k["launches"] / steps
+                k["ms_per_step"] = round(k["ms"] / steps, 4)
+                del k["ms"], k["launches"]
         return total / steps, {s: v / steps for s, v in per_stage.items()}
 
     def barrier():
@@ -224,6 +270,9 @@ def run_ours(args, rank, world, local_rank):
     afwd_ms, afwd_stages = run_phase("aabb3s", False, args.steps, args.warmup)
     afb_ms, afb_stages = run_phase("aabb3s", True, args.steps, args.warmup)
     others = {m: run_phase("quadbox_" + m, False, args.steps, args.warmup) for m in other_modes}
+    # per-kernel durations of the QuadBox forward (for the roofline)
+    fwd_kernels = {}
+    run_phase("quadbox", False, args.steps, 1, kernels=fwd_kernels)
     torch.cuda.synchronize()
     barrier()
     wall = time.time() - t_wall0
@@ -301,7 +350,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed": round(wall, 2),
     }
-    result["roofline"] = roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode)
+    result["roofline"] = roofline(fwd_stages, fwd_kernels, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode)
+    result["kernels_fwd"] = fwd_kernels
     # counted by the library at each launch, inside the timed steps of every
     # phase and of the end-to-end loop
     result["gpu_launches"] = int(launches[0])
@@ -310,76 +360,186 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
-def stage_bytes(P, n, W, H, digit_bits, sort_mode):
-    """Algorithmic HBM bytes of the emit and sort stages of one frame."""
-    tiles = ((W + 15) // 16) * ((H + 15) // 16)
-    tile_bits = (tiles - 1).bit_length()
-    if sort_mode == "chunked":
-        # no sort stage: per Gaussian the depth keys (read 20 B, write 8 B), the
-        # depth sort of n 4-byte keys + values (4 passes, 16 B each), the scan
-        # (read 8 B, write 4 B) and the segment record (64 B) read twice (count
-        # and placement); per pair one 4 B value written at its final position
-        return 0, n * (28 + 4 * 16 + 12 + 2 * 64) + 4 * P
-    if sort_mode == "depth_first":
-        # emit: depth keys (read 20 B, write 8 B per Gaussian), depth sort of n
-        # 4-byte keys + values (4 passes, 16 B each), scan (read 8 B, write
-        # 4 B), segment record read (16 B), pairs written (8 B each)
-        passes = -(-tile_bits // digit_bits)
-        emit_bytes = n * (28 + 4 * 16 + 12 + 16) + 8 * P
-        # sort: the tile-id histogram (4 B per pair), 16 B per pair for every
-        # pass but the last (read and write key and value), 12 B for the last
-        # (it writes values only; the ranges come from the per-tile counts)
-        sort_bytes = P * (4 + 16 * max(0, passes - 1) + (12 if passes >= 1 else 0))
-    else:
-        passes = -(-(31 + tile_bits) // digit_bits)
-        sort_bytes = P * (8 + passes * 24 + 8) + tiles * 8
-        emit_bytes = n * (12 + 48) + 12 * P
-    return sort_bytes, emit_bytes
+def kernel_work(P, n, n_eval):
+    """Algorithmic work per launch of each forward kernel at this frame: HBM
+    bytes (what the kernel must move at least) or FP32 operations."""
+    return {
+        "preprocess_kernel": ("hbm", n * PREPROCESS_BYTES),
+        "depth_keys_kernel": ("hbm", n * 28),            # read depth + count, write key + value
+        "sort_hist_kernel": ("hbm", n * 4),              # the depth keys once
+        "onesweep_kernel": ("hbm", n * 16),              # a depth-sort pass: key + value read and written
+        "scan_reduce_kernel": ("hbm", n * 8),
+        "scan_down_kernel": ("hbm", n * 12),
+        "emit_warp_kernel": ("hbm", P * 8 + n * 28),     # pairs written; depth order, offset, count, segments
+        "tile_count_kernel": ("hbm", P * 4),             # the tile ids once
+        "tile_sort_pass": ("hbm", P * 16),               # key + value read and written
+        "tile_sort_pass_values": ("hbm", P * 12),        # key + value read, value written
+        "render_kernel": ("alu", n_eval * RENDER_FLOPS_PER_EVAL if n_eval else 0),
+    }
 
 
-def roofline(fwd_stages, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
-    """Roofline of the dominant kernel of the forward step (see the design doc for
-    the algorithmic bytes and flops per unit)."""
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit of
+# work from the ncu captures under profiles/ (kernel -> bytes per pair), for
+# the kernels as they are now.
+TRAFFIC_PER_PAIR = {}
+
+
+def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
+    """Roofline of the dominant kernel of the forward step: its algorithmic
+    work per launch over its average launch duration, both measured in the
+    timed steps (CUDA events recorded at each launch on the launching
+    stream); every other kernel of the step is listed the same way."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sort_bytes, emit_bytes = stage_bytes(P, n, W, H, digit_bits, sort_mode)
-    pre_bytes = n * PREPROCESS_BYTES
-    stage_kernel = {"preprocess": "preprocess_kernel", "render": "render_kernel",
-                    "emit": {"chunked": "depth sort + chunk_count/scan + chunk_emit_kernel",
-                             "depth_first": "depth sort + scan + emit_warp_kernel",
-                             "full_key": "emit_warp_kernel"}[sort_mode],
-                    "sort": {"chunked": "(none: pairs placed by the emit)",
-                             "depth_first": "tile_count_kernel + onesweep_kernel (tile-sort passes)",
-                             "full_key": "onesweep_kernel (+hist, ranges)"}[sort_mode]}
-    hbm_bytes = {"preprocess": pre_bytes, "emit": emit_bytes, "sort": sort_bytes}
-    dom = max(fwd_stages, key=lambda k: fwd_stages[k])
-    out = {}
-    if dom == "render" and n_eval:
-        sm_mhz = clk.get("sm_mhz") or 1440.0
-        peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        flops = n_eval * RENDER_FLOPS_PER_EVAL
-        ach = flops / (fwd_stages["render"] * 1e-3) / 1e12
-        out = {"kernel": "render_kernel", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak_tflops, 3),
-               "unit": "TFLOP/s", "frac": round(ach / peak_tflops, 4), "traffic": None,
-               "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median sampled clock)",
-               "evaluations": n_eval}
-    else:
-        ach = hbm_bytes[dom] / (fwd_stages[dom] * 1e-3) / 1e9
-        out = {"kernel": stage_kernel[dom], "bound": "hbm", "achieved": round(ach, 1),
-               "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
-               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    # every HBM-bound stage
-    out["hbm_stages"] = {}
-    for st, b in hbm_bytes.items():
-        if b and fwd_stages.get(st, 0) > 1e-3:
-            gbs = b / (fwd_stages[st] * 1e-3) / 1e9
-            out["hbm_stages"][st] = {"kernel": stage_kernel[st], "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
-                                     "bytes": b}
-    out["dominant_stage"] = dom
+    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    work = kernel_work(P, n, n_eval)
+    rows = {}
+    for name, k in kernels.items():
+        if name not in work or not k.get("ms_per_launch"):
+            continue
+        bound, amount = work[name]
+        secs = k["ms_per_launch"] * 1e-3
+        if bound == "hbm":
+            ach = amount / secs / 1e9
+            rows[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(ach / hbm, 4), "bytes_per_launch": amount,
+                          "ms_per_launch": k["ms_per_launch"], "ms_per_step": k["ms_per_step"]}
+        elif amount:
+            ach = amount / secs / 1e12
+            rows[name] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
+                          "frac": round(ach / alu_peak, 4), "flops_per_launch": amount,
+                          "ms_per_launch": k["ms_per_launch"], "ms_per_step": k["ms_per_step"]}
+    if not rows:
+        return {"kernel": None}
+    dom = max(rows, key=lambda r: rows[r]["ms_per_step"])
+    d = rows[dom]
+    traffic = None
+    if dom in TRAFFIC_PER_PAIR:
+        traffic = int(TRAFFIC_PER_PAIR[dom] * P)
+    out = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+           "frac": d["frac"], "traffic": traffic,
+           "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if d["bound"] == "hbm" else
+                           f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median sampled SM clock)"),
+           "kernels": rows}
+    return out
+
+
+def _time_ms(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def run_c3(args, dev):
+    """Zoom sweep: 3M Gaussians at 2560x1440, 30 views from distance 40 to 2;
+    tile pairs and forward FPS per view for QuadBox and the 3-sigma AABB."""
+    import numpy as np
+    import torch
+
+    from paper_2605_04844_gb300 import _native as N
+    from paper_2605_04844_gb300 import rasterizer as R
+    from paper_2605_04844_gb300 import synth
+
+    scene_np, cams = synth.config3()
+    sd = {k: (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v) for k, v in scene_np.items()}
+    s = R.scene_struct(sd)
+    stream = torch.cuda.current_stream(dev)
+    frames = {}
+    views = []
+    for k, cam in enumerate(cams):
+        d = float(-cam["viewmat"][2][3]) if "viewmat" in cam else None
+        row = {"view": k, "distance": round(abs(d), 3) if d is not None else None}
+        cs = R.camera_struct(cam)
+        for mode in ("quadbox", "aabb3s"):
+            try:
+                _, fr = R.forward(sd, cam, mode, frame=frames.get(mode))
+            except N.QbCapacityError:
+                row[mode] = {"pairs": None, "note": "over 2^30 pairs"}
+                continue
+            frames[mode] = fr
+            pairs = fr.n_pairs
+            img = torch.empty((3, cam["height"], cam["width"]), device=dev)
+
+            def fwd(fr=fr, mode=mode):
+                fr.preprocess(s, cs, mode)
+                fr.bin_emit(sync=False)
+                fr.sort()
+                fr.render(None, img)
+            ms = _time_ms(fwd, 3, 1, stream)
+            fr.check()
+            row[mode] = {"pairs": pairs, "fwd_ms": round(ms, 3), "fps": round(1000.0 / ms, 1)}
+        if row.get("quadbox", {}).get("pairs") and row.get("aabb3s", {}).get("pairs"):
+            row["pair_ratio"] = round(row["aabb3s"]["pairs"] / max(1, row["quadbox"]["pairs"]), 3)
+            row["speedup"] = round(row["aabb3s"]["fwd_ms"] / row["quadbox"]["fwd_ms"], 3)
+        views.append(row)
+    return {"workload": "3M Gaussians (ball of radius 10 at the origin), 2560x1440, SH3, 30 views on -z from "
+                        "distance 40 to 2 (geometric)", "views": views}
+
+
+def run_c4(args, dev):
+    """500k Gaussians, 1264x832, SH3: forward + backward with an L1 loss against
+    a random target (dL/dimg = sign(img - target) / (3 H W))."""
+    import numpy as np
+    import torch
+
+    from paper_2605_04844_gb300 import _native as N
+    from paper_2605_04844_gb300 import rasterizer as R
+    from paper_2605_04844_gb300 import synth
+
+    scene_np, cam, target_np = synth.config4()
+    sd = {k: (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v) for k, v in scene_np.items()}
+    target = torch.from_numpy(target_np).to(dev)
+    s, cs = R.scene_struct(sd), R.camera_struct(cam)
+    H, W = cam["height"], cam["width"]
+    stream = torch.cuda.current_stream(dev)
+    grads = {k: torch.zeros_like(sd[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    gs = N.QbSceneGrads()
+    gs.means, gs.scales, gs.quats = grads["means"].data_ptr(), grads["scales"].data_ptr(), grads["quats"].data_ptr()
+    gs.opacities, gs.sh = grads["opacities"].data_ptr(), grads["sh"].data_ptr()
+    img = torch.empty((3, H, W), device=dev)
+    dL = torch.empty_like(img)
+    out = {"workload": "500k Gaussians, 1264x832, SH3, L1 loss against a U[0,1] target (seed 2004)"}
+    for mode in ("quadbox", "aabb3s"):
+        _, fr = R.forward(sd, cam, mode)
+        pairs = fr.n_pairs
+
+        def step(fr=fr, mode=mode):
+            fr.preprocess(s, cs, mode)
+            fr.bin_emit(sync=False)
+            fr.sort()
+            fr.render(None, img)
+            torch.sub(img, target, out=dL)
+            dL.sign_().mul_(1.0 / (3 * H * W))
+            for g in grads.values():
+                g.zero_()
+            N.qb_render_bwd(fr.frame, s, cs, None, dL, gs, None)
+
+        def fwd(fr=fr, mode=mode):
+            fr.preprocess(s, cs, mode)
+            fr.bin_emit(sync=False)
+            fr.sort()
+            fr.render(None, img)
+        fb = _time_ms(step, 10, 3, stream)
+        f = _time_ms(fwd, 10, 3, stream)
+        fr.check()
+        out[mode] = {"pairs": pairs, "fwd_ms": round(f, 3), "fwd_bwd_ms": round(fb, 3),
+                     "fwd_bwd_per_s": round(1000.0 / fb, 1)}
+    out["speedup_fwd_bwd"] = round(out["aabb3s"]["fwd_bwd_ms"] / out["quadbox"]["fwd_bwd_ms"], 3)
     return out
 
 
@@ -494,6 +654,10 @@ def run_batch(args, dev):
             "speedup_fwd": round(sep_fwd / g_fwd, 3), "speedup_fwd_bwd": round(sep_fb / g_fb, 3)}
 
 
+# GPU spin before each step of the per-kernel timing phase (~4 ms at 2 GHz):
+# longer than the host takes to queue one step with its events.
+KERNEL_TIMING_SPIN_CYCLES = 8_000_000
+
 # Algorithmic bytes of the preprocess per Gaussian: read 44 B of parameters and
 # 192 B of SH coefficients (degree 3), write mu^2D 8, conic+o 16, colour+depth
 # 16, box 16, 3-sigma radius 4, meta 4, count 4 (68 B).
@@ -541,15 +705,26 @@ def oracle_frame_seconds(scene_np, cam, row_stride=16):
 
 
 def cpu_baseline(scene_np, cam):
+    """The FP64 oracle on the host cores: the C2 frame on all cores (the
+    reported value) and on one core, and the whole C1 frame on both."""
     from oracle import oracle as O
+    from paper_2605_04844_gb300 import synth
     O.build()
+    cores = O.max_threads()
     secs, P, npx = oracle_frame_seconds(scene_np, cam)
-    cores = os.cpu_count()
-    omp = os.environ.get("OMP_NUM_THREADS")
-    return {"value": round(1.0 / secs, 5), "unit": UNIT, "cores": int(omp) if omp else cores, "kind": "oracle",
+    O.set_threads(1)
+    secs1, _, npx1 = oracle_frame_seconds(scene_np, cam, row_stride=64)
+    c1_scene, c1_cam = synth.config1()
+    c1_1 = oracle_frame_seconds(c1_scene, c1_cam, row_stride=1)[0]
+    O.set_threads(cores)
+    c1_all = oracle_frame_seconds(c1_scene, c1_cam, row_stride=1)[0]
+    return {"value": round(1.0 / secs, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one 1M-Gaussian 1920x1080 QuadBox frame: FP64 projection, binning and sort in full, "
                       f"compositing of every 16th tile row ({npx} pixels) scaled to the frame",
-            "seconds_per_frame": round(secs, 3)}
+            "seconds_per_frame": round(secs, 3),
+            "one_core_seconds_per_frame": round(secs1, 3),
+            "one_core_sample": f"the same frame with every 64th tile row composited ({npx1} pixels), scaled",
+            "c1_10k_256x256_seconds": {"all_cores": round(c1_all, 4), "one_core": round(c1_1, 4)}}
 
 
 def run_reference(args):
@@ -595,9 +770,15 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res = run_ours(args, rank, world, local_rank)
-    if rank == 0 and not args.no_batch:
+    if rank == 0:
         import torch
-        res["batch64"] = run_batch(args, torch.device("cuda", local_rank))
+        dev = torch.device("cuda", local_rank)
+        if not args.no_c4:
+            res["c4_fwd_bwd"] = run_c4(args, dev)
+        if not args.no_c3:
+            res["c3_zoom"] = run_c3(args, dev)
+        if not args.no_batch:
+            res["batch64"] = run_batch(args, dev)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             from paper_2605_04844_gb300 import synth

@@ -195,6 +195,14 @@ const char *qb_version(void);
  * threads, all devices), counted on the host at each launch. */
 uint64_t qb_kernel_launches(void);
 
+/* Instrumentation: when set, hook(kernel name, stream, user) is called on the
+ * host immediately before each kernel launch of the library, on the thread
+ * that launches it (e.g. to record a CUDA event on that stream, so kernel
+ * durations can be measured in stream order).  NULL removes it.  The hook
+ * must not call back into the library. */
+typedef void (*qb_launch_hook)(const char *kernel, qb_stream_t stream, void *user);
+void qb_set_launch_hook(qb_launch_hook hook, void *user);
+
 /* Bytes of device workspace for a frame of n Gaussians, a width x height
  * image and room for pair_capacity Gaussian-tile pairs (pair_capacity
  * <= 2^30).  Returns 0 for invalid sizes. */

@@ -69,6 +69,15 @@ def lib():
     return _lib
 
 
+def set_threads(n: int) -> None:
+    """Threads of the C oracle's OpenMP loops (for timing; results do not depend on it)."""
+    lib().orc_set_threads(ctypes.c_int(int(n)))
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
+
+
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 

@@ -30,6 +30,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_TILE 16
 #define ORC_NF 32   /* doubles per Gaussian in the projection record */
@@ -93,6 +96,25 @@ static double assoc_legendre(int l, int m, double x)
  * Condon-Shortley phase):  m<0: sqrt2 Im Y_l^|m|,  m=0: Y_l^0,
  * m>0: sqrt2 Re Y_l^m.  Coefficient index k = l*l + l + m.  d is a unit
  * vector; the angles are taken from it directly. */
+/* Threads of the OpenMP loops (timing only; results do not depend on it). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 void orc_sh_basis(int deg, const double *d, double *Y)
 {
     double z = fmax(-1.0, fmin(1.0, d[2]));

@@ -90,6 +90,7 @@ _SIGS = [
     ("qb_last_error", ctypes.c_char_p, []),
     ("qb_version", ctypes.c_char_p, []),
     ("qb_kernel_launches", c_u64, []),
+    ("qb_set_launch_hook", None, [c_vp, c_vp]),
     ("qb_frame_workspace_bytes", c_size, [c_i32, c_i32, c_i32, c_u64]),
     ("qb_frame_init", c_i32, [ctypes.POINTER(QbFrame), c_i32, c_i32, c_i32, c_u64, c_vp, c_size, c_vp]),
     ("qb_frame_arrays_get", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbFrameArrays)]),
@@ -186,6 +187,21 @@ def qb_frame_check(frame: QbFrame, stream=None):
 
 def qb_kernel_launches() -> int:
     return int(load().qb_kernel_launches())
+
+
+LAUNCH_HOOK = ctypes.CFUNCTYPE(None, ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p)
+_hook_ref = None
+
+
+def qb_set_launch_hook(fn):
+    """fn(kernel: str, stream_handle: int) or None; called before each launch."""
+    global _hook_ref
+    if fn is None:
+        load().qb_set_launch_hook(None, None)
+        _hook_ref = None
+        return
+    _hook_ref = LAUNCH_HOOK(lambda name, stream, user: fn(name.decode(), stream or 0))
+    load().qb_set_launch_hook(ctypes.cast(_hook_ref, c_vp), None)
 
 
 def qb_frame_tile_keys(frame: QbFrame, out, stream=None):

@@ -182,7 +182,13 @@ qb_status check_camera(const qb_frame *f, const qb_camera *c) {
 namespace qb {
 void set_last_error(const char *msg) { g_err = msg; }
 static std::atomic<uint64_t> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static std::atomic<qb_launch_hook> g_hook{nullptr};
+static std::atomic<void *> g_hook_user{nullptr};
+void note_launch(const char *kernel, cudaStream_t s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    const qb_launch_hook h = g_hook.load(std::memory_order_acquire);
+    if (h) h(kernel, (qb_stream_t)s, g_hook_user.load(std::memory_order_relaxed));
+}
 }  // namespace qb
 
 extern "C" {
@@ -192,6 +198,11 @@ const char *qb_last_error(void) { return g_err.c_str(); }
 const char *qb_version(void) { return "libquadbox 0.1 sm_103a"; }
 
 uint64_t qb_kernel_launches(void) { return qb::g_launches.load(std::memory_order_relaxed); }
+
+void qb_set_launch_hook(qb_launch_hook hook, void *user) {
+    qb::g_hook_user.store(user, std::memory_order_relaxed);
+    qb::g_hook.store(hook, std::memory_order_release);
+}
 
 size_t qb_frame_workspace_bytes(int32_t n, int32_t width, int32_t height, uint64_t pair_capacity) {
     Layout L;

@@ -225,9 +225,9 @@ cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_persistent_kernel, kBwdThreads, 0);
         if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
-        note_launch(), render_bwd_persistent_kernel<<<sms * (per_sm > 0 ? per_sm : 1), kBwdThreads, 0, s>>>(a);
+        note_launch("render_bwd_persistent_kernel", s), render_bwd_persistent_kernel<<<sms * (per_sm > 0 ? per_sm : 1), kBwdThreads, 0, s>>>(a);
     } else {
-        note_launch(), render_bwd_kernel<<<a.ts.total_tiles, kBwdThreads, 0, s>>>(a);
+        note_launch("render_bwd_kernel", s), render_bwd_kernel<<<a.ts.total_tiles, kBwdThreads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -444,14 +444,14 @@ cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s) 
     dim3 grid((a.n + 255) / 256), block(256);
     const bool one = a.cams.n_cams == 1;
     switch (deg) {
-    case 0: one ? (note_launch(), preprocess_bwd_kernel<0, true><<<grid, block, 0, s>>>(a))
-                : (note_launch(), preprocess_bwd_kernel<0, false><<<grid, block, 0, s>>>(a)); break;
-    case 1: one ? (note_launch(), preprocess_bwd_kernel<1, true><<<grid, block, 0, s>>>(a))
-                : (note_launch(), preprocess_bwd_kernel<1, false><<<grid, block, 0, s>>>(a)); break;
-    case 2: one ? (note_launch(), preprocess_bwd_kernel<2, true><<<grid, block, 0, s>>>(a))
-                : (note_launch(), preprocess_bwd_kernel<2, false><<<grid, block, 0, s>>>(a)); break;
-    default: one ? (note_launch(), preprocess_bwd_kernel<3, true><<<grid, block, 0, s>>>(a))
-                 : (note_launch(), preprocess_bwd_kernel<3, false><<<grid, block, 0, s>>>(a)); break;
+    case 0: one ? (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<0, true><<<grid, block, 0, s>>>(a))
+                : (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<0, false><<<grid, block, 0, s>>>(a)); break;
+    case 1: one ? (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<1, true><<<grid, block, 0, s>>>(a))
+                : (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<1, false><<<grid, block, 0, s>>>(a)); break;
+    case 2: one ? (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<2, true><<<grid, block, 0, s>>>(a))
+                : (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<2, false><<<grid, block, 0, s>>>(a)); break;
+    default: one ? (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<3, true><<<grid, block, 0, s>>>(a))
+                 : (note_launch("preprocess_bwd_kernel", s), preprocess_bwd_kernel<3, false><<<grid, block, 0, s>>>(a)); break;
     }
     return cudaGetLastError();
 }

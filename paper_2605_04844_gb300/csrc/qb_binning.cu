@@ -106,9 +106,9 @@ cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uin
                         uint64_t *n_pairs, cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(n_pairs, 0, sizeof(uint64_t), s);
     int nb = (n + kScanChunk - 1) / kScanChunk;
-    note_launch(), scan_reduce_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials);
-    note_launch(), scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nb, n_pairs);
-    note_launch(), scan_down_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials, offsets);
+    note_launch("scan_reduce_kernel", s), scan_reduce_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials);
+    note_launch("scan_partials_kernel", s), scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nb, n_pairs);
+    note_launch("scan_down_kernel", s), scan_down_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials, offsets);
     return cudaGetLastError();
 }
 
@@ -125,7 +125,7 @@ __global__ void depth_keys_kernel(int n, const float4 *rgbd, const uint32_t *cou
 cudaError_t launch_depth_keys(int n, const float4 *rgbd, const uint32_t *counts, uint32_t *keys, uint32_t *vals,
                               cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    note_launch(), depth_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, rgbd, counts, keys, vals);
+    note_launch("depth_keys_kernel", s), depth_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, rgbd, counts, keys, vals);
     return cudaGetLastError();
 }
 
@@ -404,7 +404,7 @@ static cudaError_t launch_emit_sweep_b(const EmitArgs &a, uint32_t *kout, uint32
     const uint64_t pairs = a.n_pairs_host != UINT64_MAX ? a.n_pairs_host : a.capacity;
     uint64_t blocks = (pairs + kSortTile - 1) / kSortTile;
     if (blocks == 0) blocks = 1;  // one block still flags an overflow
-    note_launch(), emit_sweep_kernel<RB, WRITE_KEYS><<<(unsigned)blocks, kSortBlock, smem, s>>>(a, kout, vout, bin_off, lookback,
+    note_launch("emit_sweep_kernel", s), emit_sweep_kernel<RB, WRITE_KEYS><<<(unsigned)blocks, kSortBlock, smem, s>>>(a, kout, vout, bin_off, lookback,
                                                                                counter, mask);
     return cudaGetLastError();
 }
@@ -472,13 +472,13 @@ template <typename KeyT>
 cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (a.mode == QB_BIN_QUADBOX_NAIVE) {
-        note_launch(), emit_naive_kernel<KeyT><<<(a.n + 255) / 256, 256, 0, s>>>(a, keys);
+        note_launch("emit_naive_kernel", s), emit_naive_kernel<KeyT><<<(a.n + 255) / 256, 256, 0, s>>>(a, keys);
     } else {
         const uint64_t pairs = a.n_pairs_host != UINT64_MAX ? a.n_pairs_host : a.capacity;
         const uint64_t warps = (pairs + kEmitChunk - 1) / kEmitChunk;
         const uint64_t blocks = (warps + kEmitWarps - 1) / kEmitWarps;
-        if (blocks > 0) note_launch(), emit_warp_kernel<KeyT><<<(unsigned)blocks, kEmitWarps * 32, 0, s>>>(a, keys);
-        else if (a.n > 0) note_launch(), emit_warp_kernel<KeyT><<<1, kEmitWarps * 32, 0, s>>>(a, keys);  // flags overflow
+        if (blocks > 0) note_launch("emit_warp_kernel", s), emit_warp_kernel<KeyT><<<(unsigned)blocks, kEmitWarps * 32, 0, s>>>(a, keys);
+        else if (a.n > 0) note_launch("emit_warp_kernel", s), emit_warp_kernel<KeyT><<<1, kEmitWarps * 32, 0, s>>>(a, keys);  // flags overflow
     }
     return cudaGetLastError();
 }
@@ -512,7 +512,7 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
     if (e != cudaSuccess || n_max == 0) return e;
     uint64_t blocks = (n_max + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    note_launch(), ranges_kernel<KeyT><<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges, (uint32_t)ntiles);
+    note_launch("ranges_kernel", s), ranges_kernel<KeyT><<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges, (uint32_t)ntiles);
     return cudaGetLastError();
 }
 
@@ -866,7 +866,7 @@ __global__ void __launch_bounds__(kBandWarps * 32) chunk_emit_kernel(EmitArgs e,
 cudaError_t launch_chunked(const EmitArgs &e, const ChunkArgs &a, uint2 *ranges, cudaStream_t s) {
     const int T = a.tiles_x * a.tiles_y;
     if (e.n == 0 || T == 0) return cudaSuccess;
-    note_launch(), chunk_start_kernel<<<(a.n_chunks + 1 + 255) / 256, 256, 0, s>>>(e.offsets, e.n, a.n_chunks,
+    note_launch("chunk_start_kernel", s), chunk_start_kernel<<<(a.n_chunks + 1 + 255) / 256, 256, 0, s>>>(e.offsets, e.n, a.n_chunks,
                                                                                 a.chunk_pairs, e.n_pairs, a.start);
     const size_t smem_count = (size_t)kBandWarps * a.band_diff_ints * 4;
     const size_t smem_emit = (size_t)kBandWarps * ((size_t)a.band_words * 4 + sizeof(SegTable));
@@ -884,15 +884,15 @@ cudaError_t launch_chunked(const EmitArgs &e, const ChunkArgs &a, uint2 *ranges,
             return err;
         set_emit = smem_emit;
     }
-    note_launch(), chunk_gather_kernel<<<(e.n + 255) / 256, 256, 0, s>>>(a, e.n);
+    note_launch("chunk_gather_kernel", s), chunk_gather_kernel<<<(e.n + 255) / 256, 256, 0, s>>>(a, e.n);
     const dim3 bg((a.n_bands + kBandWarps - 1) / kBandWarps, a.n_chunks);
-    note_launch(), chunk_count_kernel<<<bg, kBandWarps * 32, smem_count, s>>>(a);
+    note_launch("chunk_count_kernel", s), chunk_count_kernel<<<bg, kBandWarps * 32, smem_count, s>>>(a);
     const dim3 tg((T + 255) / 256, a.n_segs);
-    note_launch(), chunk_part_kernel<<<tg, 256, 0, s>>>(a);
-    note_launch(), chunk_tile_scan_kernel<<<(T + 255) / 256, 256, 0, s>>>(a);
-    note_launch(), chunk_ranges_kernel<<<1, 1024, 0, s>>>(a, ranges);
-    note_launch(), chunk_base_kernel<<<tg, 256, 0, s>>>(a);
-    note_launch(), chunk_emit_kernel<<<bg, kBandWarps * 32, smem_emit, s>>>(e, a);
+    note_launch("chunk_part_kernel", s), chunk_part_kernel<<<tg, 256, 0, s>>>(a);
+    note_launch("chunk_tile_scan_kernel", s), chunk_tile_scan_kernel<<<(T + 255) / 256, 256, 0, s>>>(a);
+    note_launch("chunk_ranges_kernel", s), chunk_ranges_kernel<<<1, 1024, 0, s>>>(a, ranges);
+    note_launch("chunk_base_kernel", s), chunk_base_kernel<<<tg, 256, 0, s>>>(a);
+    note_launch("chunk_emit_kernel", s), chunk_emit_kernel<<<bg, kBandWarps * 32, smem_emit, s>>>(e, a);
     return cudaGetLastError();
 }
 
@@ -925,7 +925,7 @@ __global__ void expand_ranges_kernel(const uint2 *ranges, uint32_t ntiles, uint3
 
 cudaError_t launch_expand_ranges(const uint2 *ranges, int ntiles, uint32_t *out, uint64_t n_out, cudaStream_t s) {
     if (ntiles <= 0 || n_out == 0) return cudaSuccess;
-    note_launch(), expand_ranges_kernel<<<ntiles < 65535 ? ntiles : 65535, 256, 0, s>>>(ranges, (uint32_t)ntiles, out, n_out);
+    note_launch("expand_ranges_kernel", s), expand_ranges_kernel<<<ntiles < 65535 ? ntiles : 65535, 256, 0, s>>>(ranges, (uint32_t)ntiles, out, n_out);
     return cudaGetLastError();
 }
 
@@ -975,7 +975,7 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
     uint64_t blocks = (n_max / 4 + 511) / 512;
     if (blocks > (uint64_t)sms * 2) blocks = (uint64_t)sms * 2;
     if (blocks == 0) blocks = 1;
-    note_launch(), tile_count_kernel<<<(unsigned)blocks, 512, smem, s>>>(keys, n_max, n_dev, (uint32_t)ntiles, counts);
+    note_launch("tile_count_kernel", s), tile_count_kernel<<<(unsigned)blocks, 512, smem, s>>>(keys, n_max, n_dev, (uint32_t)ntiles, counts);
     return cudaGetLastError();
 }
 
@@ -1081,7 +1081,7 @@ cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint3
         off.single[c] = c < ts.n_cams ? single_off[c] : 0u;
     }
     const size_t smem = (size_t)passes * ((size_t)1 << digit_bits) * 4;
-    note_launch(), tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, counts, ts, off, ranges, hist,
+    note_launch("tile_prep_kernel", s), tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, counts, ts, off, ranges, hist,
                                                           hist_stride, digit_bits, g, capacity);
     return cudaGetLastError();
 }

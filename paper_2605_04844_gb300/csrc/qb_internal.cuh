@@ -55,8 +55,9 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Sets the message qb_last_error() returns on the calling thread.
 void set_last_error(const char *msg);
-// Counts one kernel launch of the library (qb_kernel_launches).
-void note_launch();
+// Counts one kernel launch of the library (qb_kernel_launches) and reports
+// it to the launch hook, if one is set, just before the launch on stream s.
+void note_launch(const char *kernel, cudaStream_t s);
 
 // ---- sort -------------------------------------------------------------------
 // Digit geometry of an LSD radix sort on bits [0, end_bit) with digits of at

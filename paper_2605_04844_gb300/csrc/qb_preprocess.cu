@@ -160,10 +160,10 @@ cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     dim3 grid((a.n + 255) / 256, a.cams.n_cams), block(256);
     switch (deg) {
-    case 0: note_launch(), preprocess_kernel<0><<<grid, block, 0, s>>>(a); break;
-    case 1: note_launch(), preprocess_kernel<1><<<grid, block, 0, s>>>(a); break;
-    case 2: note_launch(), preprocess_kernel<2><<<grid, block, 0, s>>>(a); break;
-    default: note_launch(), preprocess_kernel<3><<<grid, block, 0, s>>>(a); break;
+    case 0: note_launch("preprocess_kernel", s), preprocess_kernel<0><<<grid, block, 0, s>>>(a); break;
+    case 1: note_launch("preprocess_kernel", s), preprocess_kernel<1><<<grid, block, 0, s>>>(a); break;
+    case 2: note_launch("preprocess_kernel", s), preprocess_kernel<2><<<grid, block, 0, s>>>(a); break;
+    default: note_launch("preprocess_kernel", s), preprocess_kernel<3><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

@@ -156,9 +156,9 @@ static cudaError_t launch_render_b(const RenderArgs &a, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<BATCH>, kRenderThreads, 0);
         if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
-        note_launch(), render_persistent_kernel<BATCH><<<sms * (per_sm > 0 ? per_sm : 1), kRenderThreads, 0, s>>>(a);
+        note_launch("render_persistent_kernel", s), render_persistent_kernel<BATCH><<<sms * (per_sm > 0 ? per_sm : 1), kRenderThreads, 0, s>>>(a);
     } else {
-        note_launch(), render_kernel<BATCH><<<a.ts.total_tiles, kRenderThreads, 0, s>>>(a);
+        note_launch("render_kernel", s), render_kernel<BATCH><<<a.ts.total_tiles, kRenderThreads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(const KeyT *__rest
 template <int RB, typename KeyT, bool WRITE_KEYS>
 static cudaError_t launch_pass_t(const KeyT *kin, const uint32_t *vin, KeyT *kout, uint32_t *vout, uint64_t n_max,
                                  const uint64_t *n_dev, const uint32_t *bin_off, uint32_t *lookback,
-                                 uint32_t *counter, int shift, uint32_t mask, uint32_t *err, cudaStream_t s) {
+                                 uint32_t *counter, int shift, uint32_t mask, uint32_t *err, const char *name,
+                                 cudaStream_t s) {
     static bool attrs = false;
     constexpr size_t smem = sweep_smem<RB, KeyT>();
     if (!attrs) {
@@ -144,7 +145,7 @@ static cudaError_t launch_pass_t(const KeyT *kin, const uint32_t *vin, KeyT *kou
         if (e != cudaSuccess) return e;
         attrs = true;
     }
-    note_launch(), onesweep_kernel<RB, KeyT, WRITE_KEYS><<<(unsigned)sort_tiles(n_max), kSortBlock, smem, s>>>(
+    note_launch(name, s), onesweep_kernel<RB, KeyT, WRITE_KEYS><<<(unsigned)sort_tiles(n_max), kSortBlock, smem, s>>>(
         kin, vin, kout, vout, n_max, n_dev, bin_off, lookback, counter, shift, mask, err);
     return cudaGetLastError();
 }
@@ -154,14 +155,14 @@ template <typename KeyT>
 static cudaError_t launch_pass(const KeyT *kin, const uint32_t *vin, KeyT *kout, uint32_t *vout, uint64_t n_max,
                                const uint64_t *n_dev, const uint32_t *bin_off, uint32_t *lookback,
                                uint32_t *counter, int shift, int bits, uint32_t *err, bool write_keys,
-                               cudaStream_t s) {
+                               const char *name, cudaStream_t s) {
     const uint32_t mask = (1u << bits) - 1u;
 #define QB_PASS_CASE(RB)                                                                                          \
     case RB:                                                                                                      \
         return write_keys ? launch_pass_t<RB, KeyT, true>(kin, vin, kout, vout, n_max, n_dev, bin_off, lookback,  \
-                                                          counter, shift, mask, err, s)                           \
+                                                          counter, shift, mask, err, name, s)                     \
                           : launch_pass_t<RB, KeyT, false>(kin, vin, kout, vout, n_max, n_dev, bin_off, lookback, \
-                                                           counter, shift, mask, err, s);
+                                                           counter, shift, mask, err, name, s);
     switch (bits < 4 ? 4 : bits) {
         QB_PASS_CASE(4)
         QB_PASS_CASE(5)
@@ -201,15 +202,15 @@ static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
         size_t smem = 0;
         for (int p = 0; p < g.passes; ++p) smem += (size_t)4 << g.bits[p];
         uint64_t hblocks = std::min<uint64_t>((n_max + 255) / 256, 152 * 4);
-        note_launch(), sort_hist_kernel<KeyT><<<(unsigned)hblocks, 256, smem, s>>>(keys, n_max, n_dev, g, hist);
-        note_launch(), sort_hist_scan_kernel<<<g.passes, 1024, 0, s>>>(hist, g);
+        note_launch("sort_hist_kernel", s), sort_hist_kernel<KeyT><<<(unsigned)hblocks, 256, smem, s>>>(keys, n_max, n_dev, g, hist);
+        note_launch("sort_hist_scan_kernel", s), sort_hist_scan_kernel<<<g.passes, 1024, 0, s>>>(hist, g);
     }
     KeyT *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     for (int p = 0; p < g.passes; ++p) {
         e = launch_pass<KeyT>(kin, vin, kout, vout, n_max, n_dev, hist + p * kHistStride,
                               sort_lookback(scratch, n_max, digit_bits, p), sort_counter(scratch, p), g.shift[p],
-                              g.bits[p], err, true, s);
+                              g.bits[p], err, true, "onesweep_kernel", s);
         if (e != cudaSuccess) return e;
         std::swap(kin, kout);
         std::swap(vin, vout);
@@ -248,7 +249,8 @@ cudaError_t tile_sort_passes(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t 
         const uint32_t *kin = to_a ? kB : kA, *vin = to_a ? vB : vA;
         e = launch_pass<uint32_t>(kin, vin, kout, vout, n_max, n_dev, hist + p * kHistStride,
                                   sort_lookback(scratch, n_cap, digit_bits, p), sort_counter(scratch, p), g.shift[p],
-                                  g.bits[p], err, p + 1 < g.passes, s);
+                                  g.bits[p], err, p + 1 < g.passes,
+                                  p + 1 < g.passes ? "tile_sort_pass" : "tile_sort_pass_values", s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

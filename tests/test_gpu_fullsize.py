@@ -1,0 +1,105 @@
+"""Parity at the full benchmark size: 1M Gaussians, 1920x1080, SH degree 3,
+QuadBox binning, in the frame configuration the benchmark times (depth-first
+order, 8-bit digits, no host synchronisation inside the frame).
+
+Checked against the FP64 oracle: the projection of every Gaussian; every
+Gaussian's tile count, the sorted keys, values and per-tile ranges in full
+(the oracle's integer traversal fed the GPU's float32 boxes); and the image
+on a sample of tiles (the oracle's own FP64 binning and compositing, pixel by
+pixel).  The backward is checked at reduced sizes (test_gpu_backward.py): the
+oracle's plain differentiation is quadratic in the list length."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_04844_gb300 import synth
+
+from gpu_util import f64, oracle_keys_from_gpu_boxes, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full_frame():
+    import torch
+    from paper_2605_04844_gb300 import rasterizer as R
+    scene, cam = synth.config2()
+    sd = to_device(scene)
+    _, fr0 = R.forward(sd, cam, "quadbox")  # sizes the pair buffers
+    fr = R.Frame(len(scene["opacities"]), cam["width"], cam["height"], int(fr0.n_pairs * 1.1) + 4096)
+    fr.set_tuning(digit_bits=8, sort_mode="depth_first")
+    s, c = R.scene_struct(sd), R.camera_struct(cam)
+    fr.preprocess(s, c, "quadbox")
+    fr.bin_emit(sync=False)
+    fr.sort()
+    img = fr.render(None)
+    torch.cuda.synchronize()
+    fr.check()
+    P = int(fr.arrays(n_pairs=1)["counts"].to(torch.int64).sum().item())
+    A = {k: v.cpu().numpy() for k, v in fr.arrays(n_pairs=P).items()}
+    return scene, cam, img.cpu().numpy(), A, P
+
+
+def test_fullsize_preprocess(full_frame):
+    scene, cam, img, A, P = full_frame
+    ref = O.project(f64(scene), cam)
+    vis_g = (A["meta"] & 1) != 0
+    vis_o = ref[:, O.F_VALID] != 0
+    assert (vis_g != vis_o).sum() <= len(vis_g) // 5000
+    m = vis_g & vis_o
+    r = ref[m]
+    np.testing.assert_allclose(A["xy"][m], r[:, [O.F_X, O.F_Y]], rtol=1e-5, atol=1e-3)
+    con = A["conic_o"][m, :3].astype(np.float64)
+    conr = r[:, [O.F_A, O.F_B, O.F_C]]
+    scale = np.maximum(np.abs(conr[:, 0]), np.abs(conr[:, 2]))[:, None]
+    e = np.abs(con - conr) / scale
+    assert np.quantile(e, 0.999) <= 1e-5 and e.max() <= 1e-4
+    ext = A["box"][m].astype(np.float64)
+    extr = r[:, [O.F_XMAX, O.F_YMAX, O.F_XMIN, O.F_YMIN]]
+    e = np.abs(ext - extr) / extr
+    assert np.quantile(e, 0.999) <= 1e-5 and e.max() <= 1e-4
+
+
+def test_fullsize_keys_values_ranges_bit_exact(full_frame):
+    scene, cam, img, A, P = full_frame
+    W, H = cam["width"], cam["height"]
+    assert P > 10_000_000
+    o = oracle_keys_from_gpu_boxes(A, O.QUADBOX, True, W, H)
+    np.testing.assert_array_equal(A["counts"].astype(np.int64), o["counts"])
+    assert len(o["keys"]) == P
+    np.testing.assert_array_equal(_full_keys(A), o["keys"])
+    np.testing.assert_array_equal(A["vals"].astype(np.uint32), o["vals"])
+    np.testing.assert_array_equal(A["ranges"].astype(np.int64), o["ranges"])
+
+
+def _full_keys(A):
+    d = A["rgbd"][:, 3].astype(np.float32).view(np.uint32).astype(np.uint64) & np.uint64(0x7FFFFFFF)
+    tiles = A["tile_keys"].view(np.uint32).astype(np.uint64)
+    return (tiles << np.uint64(31)) | d[A["vals"].view(np.uint32).astype(np.int64)]
+
+
+def test_fullsize_image_on_sampled_tiles(full_frame):
+    scene, cam, img, A, P = full_frame
+    W, H = cam["width"], cam["height"]
+    proj = O.project(f64(scene), cam)
+    L = O.own_lists(proj, W, H, O.QUADBOX, True)
+    tx, ty = (W + 15) // 16, (H + 15) // 16
+    rng = np.random.default_rng(7)
+    tiles = rng.choice(tx * ty, size=48, replace=False)
+    tiles = np.concatenate([tiles, [0, tx - 1, tx * ty - 1, (ty - 1) * tx]])  # corners, ragged last row
+    pxs, pys = [], []
+    for t in tiles:
+        x0, y0 = (t % tx) * 16, (t // tx) * 16
+        ys, xs = np.meshgrid(np.arange(y0, min(H, y0 + 16)), np.arange(x0, min(W, x0 + 16)), indexing="ij")
+        pxs.append(xs.ravel())
+        pys.append(ys.ravel())
+    pxs, pys = np.concatenate(pxs), np.concatenate(pys)
+    rgb, T, nc, amb = O.render_pixels(W, H, pxs, pys, L["ranges"], L["vals"], proj)
+    got = img[:, pys, pxs].T.astype(np.float64)
+    diff = np.abs(got - rgb).max(axis=1)
+    amb = amb != 0
+    bad = diff > 2e-3
+    assert not (bad & ~amb).any(), int((bad & ~amb).sum())
+    assert (bad & amb).sum() <= max(1, int(1e-4 * len(pxs)))
+    keep = ~(bad & amb)
+    assert np.abs(got - rgb)[keep].mean() <= 1e-5
