@@ -379,9 +379,16 @@ def kernel_work(P, n, n_eval):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit of
-# work from the ncu captures under profiles/ (kernel -> bytes per pair), for
-# the kernels as they are now.
-TRAFFIC_PER_PAIR = {}
+# work, from the ncu --set full captures of the 600k-Gaussian 1080p frame
+# (20,633,099 pairs, 398,728,138 evaluations) summarised under profiles/,
+# scaled to a launch of this frame by its units; valid for the kernels as
+# captured (kernel -> (unit, bytes per unit)).
+TRAFFIC_PER_UNIT = {
+    "render_kernel": ("eval", (14.689792e6 + 1.715968e6) / 398728138),
+    "tile_sort_pass": ("pair", (166.880512e6 + 108.135680e6) / 20633099),
+    "tile_sort_pass_values": ("pair", (165.924096e6 + 25.264640e6) / 20633099),
+    "emit_warp_kernel": ("pair", (54.273536e6 + 117.514496e6) / 20633099),
+}
 
 
 def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
@@ -419,8 +426,10 @@ def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode
     dom = max(rows, key=lambda r: rows[r]["ms_per_step"])
     d = rows[dom]
     traffic = None
-    if dom in TRAFFIC_PER_PAIR:
-        traffic = int(TRAFFIC_PER_PAIR[dom] * P)
+    if dom in TRAFFIC_PER_UNIT:
+        unit, per = TRAFFIC_PER_UNIT[dom]
+        units = n_eval if unit == "eval" else P
+        traffic = int(per * units) if units else None
     out = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
            "frac": d["frac"], "traffic": traffic,
            "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if d["bound"] == "hbm" else
