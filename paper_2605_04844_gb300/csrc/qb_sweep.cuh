@@ -21,6 +21,7 @@ namespace qb {
 constexpr int kSortBlock = 512;
 constexpr int kSortWarps = kSortBlock / 32;
 constexpr int kSortItems = 8;
+constexpr int kSortBlocksPerSM = 3;  // resident pass blocks per SM the registers are sized for (32-bit keys)
 constexpr int kSortTile = kSortBlock * kSortItems;  // 4096 keys per block
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookWindow = 8;  // status words fetched per look-back step
@@ -93,12 +94,14 @@ constexpr size_t sweep_smem() {
 }
 
 // One pass over the tile `tile` (positions [tbase, tbase + kSortTile) of n) on the
-// digit (key >> shift) & mask, mask < 2^RB.  bin_off: the pass's exclusive
+// digit (key >> shift) & mask, mask < 2^RB.  val(k) gives item k's value; it
+// is asked for only at the scatter, after the ranking (so a caller can load
+// values late and keep fewer registers live).  bin_off: the pass's exclusive
 // bucket offsets; lookback: the pass's status words [tiles][2^RB].  With
 // WRITE_KEYS false only the values are written (the last pass, whose keys are
 // implied by the per-tile ranges).
-template <int RB, typename KeyT, bool WRITE_KEYS>
-__device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const uint32_t (&val)[kSortItems],
+template <int RB, typename KeyT, bool WRITE_KEYS, class ValFn>
+__device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn &&val,
                                            uint32_t n, uint32_t tbase, uint32_t tile,
                                            const uint32_t *__restrict__ bin_off, uint32_t *lookback, int shift,
                                            uint32_t mask, uint32_t *err, KeyT *__restrict__ kout,
@@ -117,14 +120,13 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
     const uint32_t wbase = tbase + (uint32_t)wid * (32 * kSortItems);
     // items of this warp that exist: item k of lane l is valid when 32 k + l < wcount
     const int wcount = n > wbase ? (int)min(n - wbase, (uint32_t)(32 * kSortItems)) : 0;
-    uint32_t dig[kSortItems], rank[kSortItems];
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) dig[k] = (uint32_t)(key[k] >> shift) & mask;
+    uint32_t rank[kSortItems];
+    auto dig = [&](int k) { return (uint32_t)(key[k] >> shift) & mask; };
 
     // ---- early digit counts of the tile ----
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k)
-        if (32 * k + lane < wcount) atomicAdd(&s_bcount[dig[k]], 1u);
+        if (32 * k + lane < wcount) atomicAdd(&s_bcount[dig(k)], 1u);
     __syncthreads();
 
     // ---- publish this tile's counts, prefetch the look-back ----
@@ -160,7 +162,7 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const bool valid = 32 * k + lane < wcount;
-        const uint32_t d = valid ? dig[k] : (uint32_t)R;
+        const uint32_t d = valid ? dig(k) : (uint32_t)R;
         uint32_t peers = 0xffffffffu;
 #pragma unroll
         for (int b = 0; b <= RB; ++b) {
@@ -251,8 +253,8 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
 #pragma unroll
         for (int k = 0; k < kSortItems; ++k) {
             if (32 * k + lane < wcount) {
-                const uint32_t d = dig[k];
-                s_pairs[s_lstart[d] + s_whist[wid * R + d] + rank[k]] = make_uint2((uint32_t)key[k], val[k]);
+                const uint32_t d = dig(k);
+                s_pairs[s_lstart[d] + s_whist[wid * R + d] + rank[k]] = make_uint2((uint32_t)key[k], val(k));
             }
         }
         __syncthreads();
@@ -276,7 +278,7 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
 #pragma unroll
         for (int k = 0; k < kSortItems; ++k) {
             if (32 * k + lane < wcount) {
-                const uint32_t d = dig[k];
+                const uint32_t d = dig(k);
                 const uint32_t lr = s_lstart[d] + s_whist[wid * R + d] + rank[k];
                 s_keys[lr] = key[k];
                 rank[k] = lr;
@@ -298,7 +300,7 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], const 
         // ---- values through the same permutation ----
 #pragma unroll
         for (int k = 0; k < kSortItems; ++k)
-            if (32 * k + lane < wcount) s_vals[rank[k]] = val[k];
+            if (32 * k + lane < wcount) s_vals[rank[k]] = val(k);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kSortItems; ++k) {
