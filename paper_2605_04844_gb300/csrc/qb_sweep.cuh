@@ -18,10 +18,10 @@
 
 namespace qb {
 
-constexpr int kSortBlock = 512;
+constexpr int kSortBlock = 256;
 constexpr int kSortWarps = kSortBlock / 32;
-constexpr int kSortItems = 8;
-constexpr int kSortBlocksPerSM = 3;  // resident pass blocks per SM the registers are sized for (32-bit keys)
+constexpr int kSortItems = 16;
+constexpr int kSortBlocksPerSM = 5;  // resident pass blocks per SM the registers are sized for (32-bit keys)
 constexpr int kSortTile = kSortBlock * kSortItems;  // 4096 keys per block
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookWindow = 8;  // status words fetched per look-back step
