@@ -2,9 +2,9 @@
 // differentiable rasteriser (Sec. 4.1 states the rasteriser is differentiable;
 // the gradients below differentiate Eq. 2 and the Sec. 2 projection).
 //
-// K7: a 128-thread block per tile (two pixels of a column per thread) walks
-// the tile list in reverse, from the largest last-contributor position of its
-// pixels down to 0.  Each pixel recomputes alpha exactly as the forward did and the
+// K7: a 64-thread block per tile (four pixels of a column per thread, rows
+// r, r+4, r+8, r+12) walks the tile list in reverse, from the largest
+// last-contributor position of its pixels down to 0.  Each pixel recomputes alpha exactly as the forward did and the
 // transmittance by division, T_k = T_{k+1} / (1 - alpha_k), keeping the colour
 // behind the current entry, B_k = sum_{i>k} T_i alpha_i c_i + T_final bg:
 //   dC/dc_k     = T_k alpha_k
@@ -25,7 +25,8 @@
 
 namespace qb {
 
-constexpr int kBwdThreads = kTile * kTile / 2;  // two pixels per thread
+constexpr int kBwdPix = 4;                            // pixels per thread (one column)
+constexpr int kBwdThreads = kTile * kTile / kBwdPix;  // 64
 constexpr int kBwdBatch = 256;                  // entries staged per shared-memory batch
 
 // float -> double by rebuilding the IEEE-754 bit pattern with integer
@@ -121,8 +122,8 @@ __device__ __forceinline__ void bwd_pixel(BwdPix &q, int p, float4 m, float4 c, 
     }
 }
 
-// A tile by kBwdThreads threads, each owning two pixels of one column (rows r
-// and r + 8), like the forward.
+// A tile by kBwdThreads threads, each owning kBwdPix pixels of one column
+// (rows r, r + 4, r + 8, r + 12), like the forward.
 __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile, int ci, uint32_t *s_id, float4 *s_m,
                                                 float4 *s_c, float4 *s_rgb, int *s_maxlast) {
     const CamTile &C = a.ts.cam[ci];
@@ -130,18 +131,21 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
     const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31;
     const int px = tx * kTile + (tid & (kTile - 1));
-    const int py0 = ty * kTile + (tid >> kTileShift), py1 = py0 + 8;
-    const float pxf = (float)px, py0f = (float)py0, py1f = (float)py1;
+    const int py_first = ty * kTile + (tid >> kTileShift);
+    const float pxf = (float)px;
     const size_t plane = (size_t)C.W * C.H;
     const float *dl = a.dL_dimg + 3 * C.pix_base;
 
-    BwdPix q[2];
-    const int pys[2] = {py0, py1};
+    BwdPix q[kBwdPix];
+    float pyf[kBwdPix];
+    int mylast = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kBwdPix; ++h) {
+        const int py = py_first + h * (kTile / kBwdPix);
+        pyf[h] = (float)py;
         q[h] = BwdPix{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
-        if (px < C.W && pys[h] < C.H) {
-            const size_t pix = (size_t)pys[h] * C.W + px;
+        if (px < C.W && py < C.H) {
+            const size_t pix = (size_t)py * C.W + px;
             q[h].T = a.tfinal[C.pix_base + pix];
             q[h].last = a.ncontrib[C.pix_base + pix];
             q[h].g0 = dl[pix];
@@ -151,10 +155,10 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
         q[h].B0 = q[h].T * a.bg[0];
         q[h].B1 = q[h].T * a.bg[1];
         q[h].B2 = q[h].T * a.bg[2];
+        mylast = max(mylast, q[h].last);
     }
     if (tid == 0) *s_maxlast = 0;
     __syncthreads();
-    const int mylast = max(q[0].last, q[1].last);
     if (mylast > 0) atomicMax(s_maxlast, mylast);
     __syncthreads();
     const int maxlast = *s_maxlast;
@@ -185,8 +189,8 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
                 const float dx = m.x - pxf;
                 float A, Bt;
                 power_terms(c.x, c.y, dx, A, Bt);
-                bwd_pixel(q[0], p, m, c, rgb, dx, A, Bt, py0f, gv, contrib);
-                bwd_pixel(q[1], p, m, c, rgb, dx, A, Bt, py1f, gv, contrib);
+#pragma unroll
+                for (int h = 0; h < kBwdPix; ++h) bwd_pixel(q[h], p, m, c, rgb, dx, A, Bt, pyf[h], gv, contrib);
             }
             if (__ballot_sync(0xffffffffu, contrib)) warp_reduce9_add(gv, a.g_screen + (size_t)s_id[j] * 9, lane);
         }

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(1024) sort_hist_scan_kernel(uint32_t *hist, Pa
 
 // One digit pass over pairs already in memory.
 template <int RB, typename KeyT, bool WRITE_KEYS>
-__global__ void __launch_bounds__(kSortBlock, sizeof(KeyT) == 4 ? kSortBlocksPerSM : 2) onesweep_kernel(const KeyT *__restrict__ kin,
+__global__ void __launch_bounds__(kSortBlock, sizeof(KeyT) == 4 ? kSortBlocksPerSM : 3) onesweep_kernel(const KeyT *__restrict__ kin,
                                                               const uint32_t *__restrict__ vin,
                                                               KeyT *__restrict__ kout, uint32_t *__restrict__ vout,
                                                               uint64_t n_max, const uint64_t *n_dev,
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(kSortBlock, sizeof(KeyT) == 4 ? kSortBlocksPer
     const uint32_t tbase = tile * kSortTile;
     if (tbase >= n) return;  // block-uniform
 
-    // warp-striped load: item k of lane l at wbase + 32k + l; with 32-bit keys
-    // the values are read only at the scatter, after the ranking
+    // warp-striped load: item k of lane l at wbase + 32k + l; the values are
+    // read only at the scatter, after the ranking
     const uint32_t wbase = tbase + (uint32_t)wid * (32 * kSortItems);
     KeyT key[kSortItems];
 #pragma unroll
@@ -123,20 +123,9 @@ __global__ void __launch_bounds__(kSortBlock, sizeof(KeyT) == 4 ? kSortBlocksPer
         const uint32_t idx = wbase + 32 * k + lane;
         key[k] = idx < n ? __ldcs(kin + idx) : KeyT(0);
     }
-    if constexpr (sizeof(KeyT) == 4) {
-        auto val = [&](int k) -> uint32_t { return __ldcs(vin + wbase + 32 * k + lane); };
-        sweep_tile<RB, KeyT, WRITE_KEYS>(key, val, n, tbase, tile, bin_off, lookback, shift, mask, err, kout, vout,
-                                         smem);
-    } else {  // 64-bit keys keep two blocks per SM: registers for the values early
-        uint32_t v[kSortItems];
-#pragma unroll
-        for (int k = 0; k < kSortItems; ++k) {
-            const uint32_t idx = wbase + 32 * k + lane;
-            v[k] = idx < n ? __ldcs(vin + idx) : 0u;
-        }
-        sweep_tile<RB, KeyT, WRITE_KEYS>(key, [&](int k) { return v[k]; }, n, tbase, tile, bin_off, lookback, shift,
-                                         mask, err, kout, vout, smem);
-    }
+    auto val = [&](int k) -> uint32_t { return __ldcs(vin + wbase + 32 * k + lane); };
+    sweep_tile<RB, KeyT, WRITE_KEYS>(key, val, n, tbase, tile, bin_off, lookback, shift, mask, err, kout, vout,
+                                     smem);
 }
 
 template <int RB, typename KeyT, bool WRITE_KEYS>
