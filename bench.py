@@ -365,7 +365,6 @@ def kernel_work(P, n, n_eval):
     bytes (what the kernel must move at least) or FP32 operations."""
     return {
         "preprocess_kernel": ("hbm", n * PREPROCESS_BYTES),
-        "depth_keys_kernel": ("hbm", n * 28),            # read depth + count, write key + value
         "sort_hist_kernel": ("hbm", n * 4),              # the depth keys once
         "onesweep_kernel": ("hbm", n * 16),              # a depth-sort pass: key + value read and written
         "scan_reduce_kernel": ("hbm", n * 8),

@@ -343,6 +343,10 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
         QB_CUDA(cudaMemsetAsync(a.tile_diff, 0, L.tile_single - L.tile_diff + 4 * (size_t)frame->tiles_x * frame->tiles_y,
                                 (cudaStream_t)stream));
     }
+    if (eff != QB_SORT_FULL_KEY) {  // the depth-order sort's keys, written by the preprocess
+        a.depth_keys = at<uint32_t>(frame, L.dkeys0);
+        a.depth_vals = at<uint32_t>(frame, L.dvals0);
+    }
     QB_CUDA(launch_preprocess(a, scene->sh_degree, (cudaStream_t)stream));
     // requested sort | effective sort << 8 | fused emit << 16, as the counts were made for
     frame->reserved[0] = frame->sort_mode | (eff << 8) | ((fused ? 1 : 0) << 16);
@@ -375,7 +379,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         // emission order = Gaussians sorted by (depth, index)
         uint32_t *dk0 = at<uint32_t>(frame, L.dkeys0), *dk1 = at<uint32_t>(frame, L.dkeys1);
         uint32_t *dv0 = at<uint32_t>(frame, L.dvals0), *dv1 = at<uint32_t>(frame, L.dvals1);
-        QB_CUDA(launch_depth_keys(frame->n, at<float4>(frame, L.rgbd), at<uint32_t>(frame, L.counts), dk0, dv0, s));
+        // (keys and indices in dk0 / dv0 from the preprocess)
         int passes = 0;
         if (frame->n > 0)
             QB_CUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)frame->n, nullptr, kDepthBits, 8,

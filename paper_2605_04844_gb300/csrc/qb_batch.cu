@@ -323,11 +323,12 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
             a.diff_off[c] = v.diff_off[c];
             a.single_off[c] = v.single_off[c];
         }
-        QB_BCUDA(launch_preprocess(a, scene->sh_degree, s));
-        // ---- depth order of the records, scan in that order ----
         uint32_t *dk0 = bat<uint32_t>(b, L.dk0), *dk1 = bat<uint32_t>(b, L.dk1);
         uint32_t *dv0 = bat<uint32_t>(b, L.dv0), *dv1 = bat<uint32_t>(b, L.dv1);
-        QB_BCUDA(launch_depth_keys(nrec, a.rgbd, a.counts, dk0, dv0, s));
+        a.depth_keys = dk0;  // the depth-order sort's keys, written by the preprocess
+        a.depth_vals = dv0;
+        QB_BCUDA(launch_preprocess(a, scene->sh_degree, s));
+        // ---- depth order of the records, scan in that order ----
         int passes = 0;
         if (nrec > 0)
             QB_BCUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)nrec, nullptr, kDepthBits, 8, bat<void>(b, L.dsort),

@@ -112,22 +112,6 @@ cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uin
     return cudaGetLastError();
 }
 
-// Depth keys for the depth-first path: the float bits of the view depth of
-// every Gaussian that has tiles (positive floats order like their bits);
-// Gaussians without tiles sort last.
-__global__ void depth_keys_kernel(int n, const float4 *rgbd, const uint32_t *counts, uint32_t *keys, uint32_t *vals) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    keys[i] = counts[i] ? (__float_as_uint(rgbd[i].w) & 0x7fffffffu) : 0x7fffffffu;
-    vals[i] = (uint32_t)i;
-}
-
-cudaError_t launch_depth_keys(int n, const float4 *rgbd, const uint32_t *counts, uint32_t *keys, uint32_t *vals,
-                              cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    note_launch("depth_keys_kernel", s), depth_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, rgbd, counts, keys, vals);
-    return cudaGetLastError();
-}
 
 template <typename KeyT>
 __device__ __forceinline__ KeyT make_key(uint32_t tile, uint32_t dbits);

@@ -31,6 +31,7 @@ struct PreArgs {
     int *tile_single;  // per camera [tiles] pair counts of single-tile Gaussians
     uint32_t diff_off[kMaxGroupCams], single_off[kMaxGroupCams];
     uint4 *segs;       // [records][4] QPass segment records (pack_segments), or null
+    uint32_t *depth_keys, *depth_vals;  // [records] depth-sort keys and record indices, or null
 };
 
 // A Gaussian's QPass traversal as at most seven segments, packed in 16 words
@@ -161,8 +162,6 @@ cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s);
 cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uint32_t *offsets, uint64_t *partials,
                         uint64_t *n_pairs, cudaStream_t s);
 size_t scan_partials_count(int n);
-cudaError_t launch_depth_keys(int n, const float4 *rgbd, const uint32_t *counts, uint32_t *keys, uint32_t *vals,
-                              cudaStream_t s);
 template <typename KeyT>
 cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s);
 // K3 fused with the first pass of the depth-first tile sort (digit bits

@@ -35,6 +35,10 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     if (!ok) {
         a.counts[o] = 0u;
         a.meta[o] = 0;
+        if (a.depth_keys) {  // no tiles: sorts after every Gaussian that has some
+            a.depth_keys[o] = 0x7fffffffu;
+            a.depth_vals[o] = (uint32_t)o;
+        }
         return;
     }
     BoxTerms bt = box_terms(p);
@@ -154,6 +158,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     a.r3[o] = bt.r3;
     a.meta[o] = meta;
     a.counts[o] = cnt;
+    if (a.depth_keys) {
+        // the depth-order sort's input: positive float depths order like their
+        // bits; Gaussians without tiles sort last
+        a.depth_keys[o] = cnt ? (__float_as_uint(p.tz) & 0x7fffffffu) : 0x7fffffffu;
+        a.depth_vals[o] = (uint32_t)o;
+    }
 }
 
 cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s) {
