@@ -26,7 +26,7 @@
 namespace qb {
 
 constexpr int kBwdPix = 4;                            // pixels per thread (one column)
-constexpr int kBwdThreads = kTile * kTile / kBwdPix;  // 64
+constexpr int kBwdThreads = kTile * kTile / kBwdPix;  // threads per tile
 constexpr int kBwdBatch = 256;                  // entries staged per shared-memory batch
 
 // float -> double by rebuilding the IEEE-754 bit pattern with integer
