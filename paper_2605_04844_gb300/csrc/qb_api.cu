@@ -382,7 +382,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         // (keys and indices in dk0 / dv0 from the preprocess)
         int passes = 0;
         if (frame->n > 0)
-            QB_CUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)frame->n, nullptr, kDepthBits, 8,
+            QB_CUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)frame->n, nullptr, kDepthBits, kDepthDigitBits,
                                at<void>(frame, L.dsort_scratch), err, s, &passes));
         frame->depth_in_alt = passes & 1;
         perm = frame->depth_in_alt ? dv1 : dv0;

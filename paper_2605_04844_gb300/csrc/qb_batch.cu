@@ -331,7 +331,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         // ---- depth order of the records, scan in that order ----
         int passes = 0;
         if (nrec > 0)
-            QB_BCUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)nrec, nullptr, kDepthBits, 8, bat<void>(b, L.dsort),
+            QB_BCUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)nrec, nullptr, kDepthBits, kDepthDigitBits, bat<void>(b, L.dsort),
                                 err, s, &passes));
         const uint32_t *perm = (passes & 1) ? dv1 : dv0;
         QB_BCUDA(launch_scan(a.counts, perm, nrec, bat<uint32_t>(b, L.offsets), bat<uint64_t>(b, L.scan_part),

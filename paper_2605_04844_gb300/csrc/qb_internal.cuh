@@ -19,6 +19,7 @@ constexpr int kDepthBits = 31;              // key = (tile << 31) | depth bits
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 constexpr int kMaxDigitBits = 11;
+constexpr int kDepthDigitBits = 8;  // the depth-order sort: 31 bits in 4 passes (8 + 8 + 8 + 7)
 constexpr int kMaxPasses = 8;              // ceil(64 / 8)
 
 // meta bits
