@@ -280,6 +280,25 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
                         const float *d_dL_dimg, qb_scene_grads *grads, double *d_grad_screen,
                         qb_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* One optimisation step around the rasteriser (training integration).       */
+/* ------------------------------------------------------------------------ */
+
+/* L1 image loss: d_dL[i] = scale * sign(d_img[i] - d_target[i]) (0 where
+ * equal), and, when d_loss is non-NULL, *d_loss += scale * sum |img - target|
+ * (device double, accumulated; zero it first).  All device float [n].  With
+ * scale = 1 / n this is the gradient of the mean absolute error. */
+qb_status qb_l1_loss_grad(const float *d_img, const float *d_target, float *d_dL, uint64_t n, float scale,
+                          double *d_loss, qb_stream_t stream);
+
+/* Adam update (Kingma & Ba, bias-corrected) of n parameters in place, step
+ * `step` >= 1: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).  d_m and d_v
+ * are the caller's moment buffers (zero before the first step).  Apply it to
+ * the raw scene arrays with the gradients qb_render_bwd accumulates. */
+qb_status qb_adam_step(float *d_param, const float *d_grad, float *d_m, float *d_v, uint64_t n, float lr,
+                       float beta1, float beta2, float eps, int32_t step, qb_stream_t stream);
+
 /* Standalone pair sort (the sort used by qb_sort): sorts n (key, value)
  * pairs stably by key bits [0, end_bit) with the onesweep radix sort using
  * digit_bits-wide digits (8..11).  d_keys/d_vals hold the input; the result

@@ -103,6 +103,9 @@ _SIGS = [
     ("qb_render_fwd", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(c_f), c_vp, c_vp]),
     ("qb_render_bwd", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera),
                               ctypes.POINTER(c_f), c_vp, ctypes.POINTER(QbSceneGrads), c_vp, c_vp]),
+    ("qb_l1_loss_grad", c_i32, [c_vp, c_vp, c_vp, c_u64, ctypes.c_float, c_vp, c_vp]),
+    ("qb_adam_step", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, c_i32, c_vp]),
     ("qb_sort_scratch_bytes", c_size, [c_u64, c_i32, c_i32]),
     ("qb_sort_pairs", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, c_i32, c_vp, c_size,
                               ctypes.POINTER(c_i32), c_vp]),
@@ -240,6 +243,16 @@ def qb_render_bwd(frame: QbFrame, scene: QbScene, camera: QbCamera, bg, dL_dimg,
                   grad_screen=None, stream=None):
     check(load().qb_render_bwd(ctypes.byref(frame), ctypes.byref(scene), ctypes.byref(camera), _bg(bg),
                                ptr(dL_dimg), ctypes.byref(grads), ptr(grad_screen), stream_handle(stream)))
+
+
+def qb_l1_loss_grad(img, target, dL, scale, loss=None, stream=None):
+    check(load().qb_l1_loss_grad(ptr(img), ptr(target), ptr(dL), img.numel(), scale, ptr(loss),
+                                 stream_handle(stream)))
+
+
+def qb_adam_step(param, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
+    check(load().qb_adam_step(ptr(param), ptr(grad), ptr(m), ptr(v), param.numel(), lr, beta1, beta2, eps, step,
+                              stream_handle(stream)))
 
 
 def qb_sort_scratch_bytes(n, end_bit, digit_bits) -> int:

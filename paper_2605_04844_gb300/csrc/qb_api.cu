@@ -634,6 +634,23 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
     return QB_OK;
 }
 
+qb_status qb_l1_loss_grad(const float *d_img, const float *d_target, float *d_dL, uint64_t n, float scale,
+                          double *d_loss, qb_stream_t stream) {
+    if (n > 0 && (!d_img || !d_target || !d_dL)) return fail(QB_ERR_INVALID_ARG, "an array is NULL");
+    QB_CUDA(launch_l1_grad(d_img, d_target, d_dL, n, scale, d_loss, (cudaStream_t)stream));
+    return QB_OK;
+}
+
+qb_status qb_adam_step(float *d_param, const float *d_grad, float *d_m, float *d_v, uint64_t n, float lr, float beta1,
+                       float beta2, float eps, int32_t step, qb_stream_t stream) {
+    if (n > 0 && (!d_param || !d_grad || !d_m || !d_v)) return fail(QB_ERR_INVALID_ARG, "an array is NULL");
+    if (step < 1) return fail(QB_ERR_INVALID_ARG, "step must be >= 1 (got %d)", step);
+    if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return fail(QB_ERR_INVALID_ARG, "need 0 <= beta1, beta2 < 1 and eps > 0");
+    QB_CUDA(launch_adam(d_param, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream));
+    return QB_OK;
+}
+
 size_t qb_sort_scratch_bytes(uint64_t n, int32_t end_bit, int32_t digit_bits) {
     if (n > (1ull << 30)) return 0;
     size_t b = sort_scratch_bytes(n, end_bit, digit_bits);

@@ -186,6 +186,10 @@ constexpr int kTileCountMax = 24576;
 cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64_t *n_dev, int ntiles,
                               uint32_t *counts, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs &a, int batch, cudaStream_t s);
+cudaError_t launch_l1_grad(const float *img, const float *target, float *dL, uint64_t n, float scale, double *loss,
+                           cudaStream_t s);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, uint64_t n, float lr, float b1, float b2,
+                        float eps, int t, cudaStream_t s);
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, int deg, cudaStream_t s);
 

@@ -317,3 +317,61 @@ def calibrated_batch(scene, cams, mode="quadbox", group=16, headroom=1.1, tune=N
     cap = min(2 ** 30, int(max(pairs) * headroom) + 4096)
     del probe
     return Batch(n, cams, group, pair_capacity=cap)
+
+
+# Per-array Adam learning rates (3DGS's defaults for raw parameters; the mean's
+# is for a scene of unit extent).
+DEFAULT_LR = {"means": 1.6e-4, "scales": 5e-3, "quats": 1e-3, "opacities": 5e-2, "sh": 2.5e-3}
+
+
+class Trainer:
+    """Adam on the raw scene parameters against a target image with the L1
+    loss, every step in the library's kernels: forward, loss gradient,
+    backward, update.  `scene` holds the (mutable, raw) device arrays."""
+
+    KEYS = ("means", "scales", "quats", "opacities", "sh")
+
+    def __init__(self, scene, cam, mode="quadbox", lr=None, betas=(0.9, 0.999), eps=1e-15, bg=None, stream=None):
+        self.scene, self.cam, self.mode, self.bg = scene, cam, mode, bg
+        self.lr = dict(DEFAULT_LR, **(lr or {}))
+        self.betas, self.eps = betas, eps
+        self.stream = stream
+        self.scene_s, self.cam_s = scene_struct(scene), camera_struct(cam)
+        dev = scene["means"].device
+        self.grads = {k: torch.zeros_like(scene[k]) for k in self.KEYS}
+        self.m = {k: torch.zeros_like(scene[k]) for k in self.KEYS}
+        self.v = {k: torch.zeros_like(scene[k]) for k in self.KEYS}
+        self.gs = N.QbSceneGrads()
+        for k in self.KEYS:
+            setattr(self.gs, k, self.grads[k].data_ptr())
+        H, W = cam["height"], cam["width"]
+        self.img = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+        self.dL = torch.empty_like(self.img)
+        self.loss = torch.zeros((), dtype=torch.float64, device=dev)
+        _, self.frame = forward(scene, cam, mode, bg=bg)
+        self.t = 0
+
+    def step(self, target):
+        """One step; returns the loss (mean absolute error) as a device scalar
+        of the image before the update."""
+        fr, s = self.frame, self.stream
+        fr.preprocess(self.scene_s, self.cam_s, self.mode)
+        try:
+            fr.bin_emit(sync=True)
+        except N.QbCapacityError:  # the scene moved: grow the pair buffer
+            _, self.frame = forward(self.scene, self.cam, self.mode, bg=self.bg)
+            fr = self.frame
+            fr.preprocess(self.scene_s, self.cam_s, self.mode)
+            fr.bin_emit(sync=True)
+        fr.sort()
+        fr.render(self.bg, self.img)
+        self.loss.zero_()
+        N.qb_l1_loss_grad(self.img, target, self.dL, 1.0 / self.img.numel(), self.loss, s)
+        for g in self.grads.values():
+            g.zero_()
+        N.qb_render_bwd(fr.frame, self.scene_s, self.cam_s, self.bg, self.dL, self.gs, None, s)
+        self.t += 1
+        for k in self.KEYS:
+            N.qb_adam_step(self.scene[k], self.grads[k], self.m[k], self.v[k], self.lr[k], self.betas[0],
+                           self.betas[1], self.eps, self.t, s)
+        return self.loss
