@@ -499,6 +499,38 @@ def run_c3(args, dev):
                         "distance 40 to 2 (geometric)", "views": views}
 
 
+def run_modes(args, dev):
+    """The paper's ablation (Table 3) on C2: pairs per frame and forward time
+    of every binning mode on the same kernels (DualBox is not conservative:
+    its image differs by design)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_04844_gb300 import rasterizer as R
+    from paper_2605_04844_gb300 import synth
+
+    scene_np, cam = synth.config2(args.n, args.width, args.height)
+    sd = {k: (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v) for k, v in scene_np.items()}
+    s, cs = R.scene_struct(sd), R.camera_struct(cam)
+    stream = torch.cuda.current_stream(dev)
+    img = torch.empty((3, cam["height"], cam["width"]), device=dev)
+    out = {"workload": "C2 (1M Gaussians, 1920x1080, SH3), forward per binning mode, same kernels"}
+    for mode in ("aabb3s", "adr", "quadbox_naive", "quadbox", "dualbox"):
+        _, fr = R.forward(sd, cam, mode)
+        pairs = fr.n_pairs
+
+        def fwd(fr=fr, mode=mode):
+            fr.preprocess(s, cs, mode)
+            fr.bin_emit(sync=False)
+            fr.sort()
+            fr.render(None, img)
+        ms = _time_ms(fwd, 10, 3, stream)
+        fr.check()
+        out[mode] = {"pairs": pairs, "fwd_ms": round(ms, 4), "fps": round(1000.0 / ms, 1)}
+        del fr
+    return out
+
+
 def run_c4(args, dev):
     """500k Gaussians, 1264x832, SH3: forward + backward with an L1 loss against
     a random target (dL/dimg = sign(img - target) / (3 H W))."""
@@ -791,6 +823,7 @@ def main():
         dev = torch.device("cuda", local_rank)
         if not args.no_c4:
             res["c4_fwd_bwd"] = run_c4(args, dev)
+            res["binning_modes"] = run_modes(args, dev)
         if not args.no_c3:
             res["c3_zoom"] = run_c3(args, dev)
         if not args.no_batch:
