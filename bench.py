@@ -383,10 +383,11 @@ def kernel_work(P, n, n_eval):
 # scaled to a launch of this frame by its units; valid for the kernels as
 # captured (kernel -> (unit, bytes per unit)).
 TRAFFIC_PER_UNIT = {
-    "render_kernel": ("eval", (14.689792e6 + 1.715968e6) / 398728138),
-    "tile_sort_pass": ("pair", (166.880512e6 + 108.135680e6) / 20633099),
-    "tile_sort_pass_values": ("pair", (165.924096e6 + 25.264640e6) / 20633099),
-    "emit_warp_kernel": ("pair", (54.273536e6 + 117.514496e6) / 20633099),
+    "render_kernel": ("eval", (14.689024e6 + 2.035968e6) / 398728138),
+    "tile_sort_pass": ("pair", (167.909888e6 + 139.132160e6) / 20633099),
+    "tile_sort_pass_values": ("pair", (166.251264e6 + 42.776320e6) / 20633099),
+    "emit_warp_kernel": ("pair", (54.315520e6 + 117.350400e6) / 20633099),
+    "tile_count_kernel": ("pair", (82.578432e6 + 1.667840e6) / 20633099),
 }
 
 
@@ -422,13 +423,14 @@ def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode
                           "ms_per_launch": k["ms_per_launch"], "ms_per_step": k["ms_per_step"]}
     if not rows:
         return {"kernel": None}
+    for name, r in rows.items():
+        if name in TRAFFIC_PER_UNIT:
+            unit, per = TRAFFIC_PER_UNIT[name]
+            units = n_eval if unit == "eval" else P
+            r["traffic"] = int(per * units) if units else None
     dom = max(rows, key=lambda r: rows[r]["ms_per_step"])
     d = rows[dom]
-    traffic = None
-    if dom in TRAFFIC_PER_UNIT:
-        unit, per = TRAFFIC_PER_UNIT[dom]
-        units = n_eval if unit == "eval" else P
-        traffic = int(per * units) if units else None
+    traffic = d.get("traffic")
     out = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
            "frac": d["frac"], "traffic": traffic,
            "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if d["bound"] == "hbm" else
