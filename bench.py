@@ -710,8 +710,10 @@ KERNEL_TIMING_SPIN_CYCLES = 8_000_000
 
 # Algorithmic bytes of the preprocess per Gaussian: read 44 B of parameters and
 # 192 B of SH coefficients (degree 3), write mu^2D 8, conic+o 16, colour+depth
-# 16, box 16, 3-sigma radius 4, meta 4, count 4 (68 B).
-PREPROCESS_BYTES = 236 + 68
+# 16, box 16, 3-sigma radius 4, meta 4, count 4, depth-sort key and index 8
+# (76 B).  The QPass run records (16 to 64 B per visible Gaussian) are left
+# out, which understates the kernel's fraction slightly.
+PREPROCESS_BYTES = 236 + 76
 
 # FP32 operations per evaluated (pixel, Gaussian) entry of render_kernel:
 # dx, dy (2), power (3 mul + 2 fma + 1 neg-mul = 6), compare (1), exp (2:
