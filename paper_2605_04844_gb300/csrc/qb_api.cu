@@ -234,7 +234,7 @@ qb_status qb_frame_init(qb_frame *frame, int32_t n, int32_t width, int32_t heigh
     frame->key_bits = kDepthBits + tile_bits_for(frame->tiles_x * frame->tiles_y);
     frame->n_pairs = UINT64_MAX;
     frame->sort_digit_bits = 8;
-    frame->render_batch = 256;
+    frame->render_batch = 128;
     frame->sort_mode = QB_SORT_DEPTH_FIRST;
     QB_CUDA(cudaMemsetAsync(at<uint8_t>(frame, L.state), 0, 256, (cudaStream_t)stream));
     return QB_OK;
