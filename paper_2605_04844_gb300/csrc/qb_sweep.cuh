@@ -14,6 +14,8 @@
 // kErrTimeout and still publishes, so no block waits forever.
 #pragma once
 
+#include <type_traits>
+
 #include "qb_kernels.cuh"
 
 namespace qb {
@@ -129,11 +131,12 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
         if (32 * k + lane < wcount) atomicAdd(&s_bcount[dig(k)], 1u);
     __syncthreads();
 
-    // ---- publish this tile's counts, prefetch the look-back ----
+    // ---- publish this tile's counts ----
     // One status word per (tile, digit): a 2-bit flag (aggregate = the tile's
     // own count, inclusive = running total through the tile) and a 30-bit
-    // count.  The first look-back window is loaded here and consumed after the
-    // ranking, so its latency overlaps the warps' ranking work.
+    // count.  (Prefetching the first look-back window here, across the ranking,
+    // was measured slower: its registers made the pass spill at five blocks per
+    // SM.)
     uint32_t cnt[PER], tsum = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
@@ -142,40 +145,44 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
         tsum += cnt[j];
     }
     uint32_t *lb = lookback + (size_t)tile * R;
-    uint32_t pre_sv[kLookWindow];  // for this thread's first digit
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         int d = tid * PER + j;
         if (d < R) st_relaxed(lb + d, (tile == 0 ? kFlagIncl : kFlagAgg) | cnt[j]);
     }
-#pragma unroll
-    for (int w = 0; w < kLookWindow; ++w)
-        pre_sv[w] = (tid * PER < R && (int64_t)tile - 1 - w >= 0)
-                        ? ld_relaxed(lookback + (size_t)(tile - 1 - w) * R + tid * PER)
-                        : kFlagIncl;
 
     // ---- rank within the warp, in original order ----
-    // Lanes holding the same digit are found with one ballot per digit bit;
-    // invalid lanes carry the digit R (bit RB), which keeps them apart.
+    // Lanes holding the same digit are found with one ballot per digit bit:
+    // peers &= (bit ? ballot : ~ballot), written as ~(ballot ^ -bit) so that it
+    // is one three-input logic operation.  In a warp whose items are not all
+    // present, invalid lanes carry the digit R (bit RB), which keeps them apart;
+    // a full warp (every warp of every tile but the last) skips that bit.
     uint16_t *wh = s_whist + wid * R;
     const uint32_t lt = lanemask_lt();
+    auto rank_items = [&](auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        constexpr int NB = FULL ? RB : RB + 1;
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const bool valid = 32 * k + lane < wcount;
-        const uint32_t d = valid ? dig(k) : (uint32_t)R;
-        uint32_t peers = 0xffffffffu;
+        for (int k = 0; k < kSortItems; ++k) {
+            const bool valid = FULL || 32 * k + lane < wcount;
+            const uint32_t d = valid ? dig(k) : (uint32_t)R;
+            uint32_t peers = 0xffffffffu;
 #pragma unroll
-        for (int b = 0; b <= RB; ++b) {
-            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bb : ~bb;
+            for (int b = 0; b < NB; ++b) {
+                const uint32_t bit = (d >> b) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                peers &= ~(bb ^ (0u - bit));
+            }
+            const uint32_t pre = valid ? (uint32_t)wh[d] : 0u;
+            const uint32_t lower = __popc(peers & lt);
+            __syncwarp();
+            if (valid && lower == 0) wh[d] = (uint16_t)(pre + __popc(peers));
+            __syncwarp();
+            rank[k] = pre + lower;
         }
-        const uint32_t pre = valid ? (uint32_t)wh[d] : 0u;
-        const uint32_t lower = __popc(peers & lt);
-        __syncwarp();
-        if (valid && lower == 0) wh[d] = (uint16_t)(pre + __popc(peers));
-        __syncwarp();
-        rank[k] = pre + lower;
-    }
+    };
+    if (wcount == 32 * kSortItems) rank_items(std::true_type{});
+    else rank_items(std::false_type{});
 
     // ---- look back for the running totals, publish the inclusive prefix ----
     // Each thread walks back for its digits, kLookWindow words at a time
@@ -195,14 +202,11 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
             int64_t t = (int64_t)tile - 1;
             int spins = 0;
             bool done = false;
-            bool first = j == 0;
             while (!done && t >= 0) {
                 uint32_t sv[kLookWindow];
 #pragma unroll
                 for (int w = 0; w < kLookWindow; ++w)
-                    sv[w] = first ? pre_sv[w]
-                                  : ((t - w >= 0) ? ld_relaxed(lookback + (size_t)(t - w) * R + d) : kFlagIncl);
-                first = false;
+                    sv[w] = (t - w >= 0) ? ld_relaxed(lookback + (size_t)(t - w) * R + d) : kFlagIncl;
                 int used = 0;
 #pragma unroll
                 for (int w = 0; w < kLookWindow; ++w) {
