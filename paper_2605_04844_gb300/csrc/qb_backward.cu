@@ -3,13 +3,17 @@
 // the gradients below differentiate Eq. 2 and the Sec. 2 projection).
 //
 // K7: a 64-thread block per tile (four pixels of a column per thread, rows
-// r, r+4, r+8, r+12) walks the tile list in reverse, from the largest
-// last-contributor position of its pixels down to 0.  Each pixel recomputes alpha exactly as the forward did and the
-// transmittance by division, T_k = T_{k+1} / (1 - alpha_k), keeping the colour
-// behind the current entry, B_k = sum_{i>k} T_i alpha_i c_i + T_final bg:
+// r, r+4, r+8, r+12, evaluated as two pairs with the packed FP32x2
+// instructions) walks the tile list in reverse, from the largest
+// last-contributor position of its pixels down to 0.  Each pixel recomputes
+// alpha exactly as the forward did and the transmittance by division,
+// T_k = T_{k+1} / (1 - alpha_k); with B_k = sum_{i>k} T_i alpha_i c_i + T_final bg
+// the colour behind entry k,
 //   dC/dc_k     = T_k alpha_k
 //   dC/dalpha_k = T_k c_k - B_k / (1 - alpha_k)
-// alpha = min(0.99, o G), G = exp(power): zero derivative where the cap binds.
+// and B enters dL/dalpha only through S2 = sum_c dL/dC_c B_c, which is carried
+// per pixel instead of B.  alpha = min(0.99, o G), G = exp(power): zero
+// derivative where the cap binds.
 // The 9 per-Gaussian sums (mu_x, mu_y, Sigma11, Sigma12, Sigma22, o, r, g, b;
 // the covariance entries are the well-conditioned parametrisation, with
 // dL/dLambda = -Sigma dL/dSigma Sigma) are reduced over the warp by a
@@ -27,7 +31,7 @@ namespace qb {
 
 constexpr int kBwdPix = 4;                            // pixels per thread (one column)
 constexpr int kBwdThreads = kTile * kTile / kBwdPix;  // threads per tile
-constexpr int kBwdBatch = 256;                  // entries staged per shared-memory batch
+constexpr int kBwdBatch = 128;  // entries staged per shared-memory batch
 
 // float -> double by rebuilding the IEEE-754 bit pattern with integer
 // operations (exponent rebias 127 -> 1023, mantissa 23 -> 52 bits), so the
@@ -79,90 +83,85 @@ __device__ __forceinline__ void warp_reduce9_add(const float g[9], double *dst, 
     if (!(lane & 1) && ix < 3 && iw < 5 && iv < 9 && z != 0.f) atomicAdd(dst + iv, widen(z));
 }
 
-// One pixel's part of the gradient of entry (m, c, rgb) at column offset dx
-// (the column terms A, Bt shared with the thread's other pixel), added to gv.
-struct BwdPix {
-    float T, B0, B1, B2, g0, g1, g2;
-    int last;
+// Staged entries of a backward batch, laid out for the packed FP32x2
+// arithmetic (operands the pixels of a thread share are stored twice):
+//   s0 = (mu_x, mu_x, mu_y, mu_y), s1 = (ca, ca, cb, cb),
+//   s2 = (cc, cc, skip threshold, -), s3 = (r, r, g, g), s4 = (b, b, o, o),
+// with (ca, cb, cc) = (-a/2, -b, -c/2) the rescaled conic of the forward.
+struct BwdStage {
+    uint32_t *id;
+    float4 *s0, *s1, *s2, *s3, *s4;
+    int *maxlast;
 };
 
-__device__ __forceinline__ void bwd_pixel(BwdPix &q, int p, float4 m, float4 c, float4 rgb, float dx, float A, float Bt,
-                                          float pyf, float gv[9], bool &contrib) {
-    if (p >= q.last) return;
-    const float dy = m.y - pyf;
-    const float power = power_from(A, Bt, c.z, dy);
-    if (!(power <= 0.f && power >= m.z)) return;
-    const float G = __expf(power);
-    const float oG = __fmul_rn(m.w, G);
-    const float alpha = fminf(kAlphaMax, oG);
-    if (alpha < kAlphaMin) return;
-    contrib = true;
-    const float inv = __frcp_rn(1.f - alpha);
-    q.T = q.T * inv;  // transmittance in front of this entry
-    const float w = alpha * q.T;
-    gv[6] = fmaf(w, q.g0, gv[6]);
-    gv[7] = fmaf(w, q.g1, gv[7]);
-    gv[8] = fmaf(w, q.g2, gv[8]);
-    const float dalpha = q.g0 * (q.T * rgb.x - q.B0 * inv) + q.g1 * (q.T * rgb.y - q.B1 * inv) +
-                         q.g2 * (q.T * rgb.z - q.B2 * inv);
-    q.B0 = fmaf(w, rgb.x, q.B0);
-    q.B1 = fmaf(w, rgb.y, q.B1);
-    q.B2 = fmaf(w, rgb.z, q.B2);
-    if (oG < kAlphaMax) {
-        // power = -d^T Lambda d / 2 with Lambda = Sigma^-1 and u = Lambda d:
-        // dpower/dmu = -u, dpower/dSigma = u u^T / 2
-        const float dpower = dalpha * oG;
-        const float ux = -2.f * c.x * dx - c.y * dy, uy = -c.y * dx - 2.f * c.z * dy;
-        gv[5] = fmaf(G, dalpha, gv[5]);
-        gv[0] = fmaf(-dpower, ux, gv[0]);
-        gv[1] = fmaf(-dpower, uy, gv[1]);
-        gv[2] = fmaf(0.5f * dpower * ux, ux, gv[2]);
-        gv[3] = fmaf(dpower * ux, uy, gv[3]);
-        gv[4] = fmaf(0.5f * dpower * uy, uy, gv[4]);
-    }
-}
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// The per-pixel state of a pair of pixels (one packed lane each): the
+// transmittance in front of the current entry, T; -S2 with
+// S2 = sum_c dL/dC_c B_c (the colour behind the entry, B_c, only enters the
+// gradient through this sum, which is updated as S2 += w S1 when an entry of
+// weight w = alpha T is passed); and dL/dC per channel.
+struct BwdPair {
+    float2 T, nS2, g0, g1, g2, npy;
+    int last0, last1;
+};
 
 // A tile by kBwdThreads threads, each owning kBwdPix pixels of one column
-// (rows r, r + 4, r + 8, r + 12), like the forward.
-__device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile, int ci, uint32_t *s_id, float4 *s_m,
-                                                float4 *s_c, float4 *s_rgb, int *s_maxlast) {
+// (rows r, r + 4, r + 8, r + 12) as two packed pairs (r, r + 4) and
+// (r + 8, r + 12).  Per entry, for every pixel:
+//   T <- T / (1 - alpha)                       (T in front of the entry)
+//   dL/dc_k     += alpha T dL/dC
+//   dL/dalpha    = T S1 - S2 / (1 - alpha),    S1 = sum_c dL/dC_c c_k,c
+//   S2          += alpha T S1
+// and, where the opacity cap does not bind (o G < 0.99), with
+// v = -dpower/dmu = (2 ca dx + cb dy, cb dx + 2 cc dy):
+//   dL/do += G dL/dalpha, dpower = o G dL/dalpha,
+//   dL/dmu += dpower v, dL/dSigma += dpower (vx^2/2, vx vy, vy^2/2).
+// An entry a pixel does not composite takes alpha = 0 (T, S2 unchanged, no
+// contribution), so the pairs run in lock step without branches.
+__device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile, int ci, const BwdStage &S) {
     const CamTile &C = a.ts.cam[ci];
     const uint32_t lt = gtile - C.tile_base;
     const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31;
     const int px = tx * kTile + (tid & (kTile - 1));
     const int py_first = ty * kTile + (tid >> kTileShift);
-    const float pxf = (float)px;
+    const float2 npx = f2(-(float)px, -(float)px);
     const size_t plane = (size_t)C.W * C.H;
     const float *dl = a.dL_dimg + 3 * C.pix_base;
 
-    BwdPix q[kBwdPix];
-    float pyf[kBwdPix];
+    BwdPair P[2];
     int mylast = 0;
 #pragma unroll
     for (int h = 0; h < kBwdPix; ++h) {
         const int py = py_first + h * (kTile / kBwdPix);
-        pyf[h] = (float)py;
-        q[h] = BwdPix{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        float T = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        int last = 0;
         if (px < C.W && py < C.H) {
             const size_t pix = (size_t)py * C.W + px;
-            q[h].T = a.tfinal[C.pix_base + pix];
-            q[h].last = a.ncontrib[C.pix_base + pix];
-            q[h].g0 = dl[pix];
-            q[h].g1 = dl[plane + pix];
-            q[h].g2 = dl[2 * plane + pix];
+            T = a.tfinal[C.pix_base + pix];
+            last = a.ncontrib[C.pix_base + pix];
+            g0 = dl[pix];
+            g1 = dl[plane + pix];
+            g2 = dl[2 * plane + pix];
         }
-        q[h].B0 = q[h].T * a.bg[0];
-        q[h].B1 = q[h].T * a.bg[1];
-        q[h].B2 = q[h].T * a.bg[2];
-        mylast = max(mylast, q[h].last);
+        // the colour behind the last entry is the background seen through T
+        const float nS2 = -(g0 * (T * a.bg[0]) + g1 * (T * a.bg[1]) + g2 * (T * a.bg[2]));
+        BwdPair &q = P[h >> 1];
+        if (h & 1) {
+            q.T.y = T, q.nS2.y = nS2, q.g0.y = g0, q.g1.y = g1, q.g2.y = g2, q.npy.y = -(float)py, q.last1 = last;
+        } else {
+            q.T.x = T, q.nS2.x = nS2, q.g0.x = g0, q.g1.x = g1, q.g2.x = g2, q.npy.x = -(float)py, q.last0 = last;
+        }
+        mylast = max(mylast, last);
     }
-    if (tid == 0) *s_maxlast = 0;
+    if (tid == 0) *S.maxlast = 0;
     __syncthreads();
-    if (mylast > 0) atomicMax(s_maxlast, mylast);
+    if (mylast > 0) atomicMax(S.maxlast, mylast);
     __syncthreads();
-    const int maxlast = *s_maxlast;
+    const int maxlast = *S.maxlast;
     const uint32_t rstart = a.ranges[gtile].x;
+    const float2 one = f2(1.f, 1.f), two = f2(2.f, 2.f);
 
     for (int end = maxlast; end > 0; end -= kBwdBatch) {
         const int cnt = min(kBwdBatch, end);
@@ -170,45 +169,109 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
         __syncthreads();
         for (int k = tid; k < cnt; k += kBwdThreads) {
             const uint32_t g = a.vals[rstart + start + k];
-            s_id[k] = g;
+            S.id[k] = g;
             const float2 m = a.xy[g];
             const float4 co = a.conic_o[g];
-            s_m[k] = make_float4(m.x, m.y, skip_threshold(co.w), co.w);
-            s_c[k] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, 0.f);
-            s_rgb[k] = a.rgbd[g];
+            const float4 rgb = a.rgbd[g];
+            const float ca = -0.5f * co.x, cb = -co.y, cc = -0.5f * co.z;
+            S.s0[k] = make_float4(m.x, m.x, m.y, m.y);
+            S.s1[k] = make_float4(ca, ca, cb, cb);
+            S.s2[k] = make_float4(cc, cc, skip_threshold(co.w), 0.f);
+            S.s3[k] = make_float4(rgb.x, rgb.x, rgb.y, rgb.y);
+            S.s4[k] = make_float4(rgb.z, rgb.z, co.w, co.w);
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int p = start + j;
-            float gv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool contrib = false;
-            if (p < mylast) {
-                const float4 m = s_m[j];
-                const float4 c = s_c[j];
-                const float4 rgb = s_rgb[j];
-                const float dx = m.x - pxf;
-                float A, Bt;
-                power_terms(c.x, c.y, dx, A, Bt);
+            const float4 X = S.s0[j], Q = S.s1[j], K = S.s2[j];
+            const float2 dx = __fadd2_rn(f2(X.x, X.y), npx);
+            const float2 cadx = __fmul2_rn(f2(Q.x, Q.y), dx);
+            const float2 A = __fmul2_rn(cadx, dx);
+            const float2 B = __fmul2_rn(f2(Q.z, Q.w), dx);
+            const float2 cc2 = f2(K.x, K.y);
+            float2 dy[2], pw[2];
+            bool e[4];
 #pragma unroll
-                for (int h = 0; h < kBwdPix; ++h) bwd_pixel(q[h], p, m, c, rgb, dx, A, Bt, pyf[h], gv, contrib);
+            for (int r = 0; r < 2; ++r) {
+                dy[r] = __fadd2_rn(f2(X.z, X.w), P[r].npy);
+                pw[r] = __ffma2_rn(dy[r], __ffma2_rn(cc2, dy[r], B), A);
+                e[2 * r] = p < P[r].last0 && pw[r].x <= 0.f && pw[r].x >= K.z;
+                e[2 * r + 1] = p < P[r].last1 && pw[r].y <= 0.f && pw[r].y >= K.z;
             }
-            if (__ballot_sync(0xffffffffu, contrib)) warp_reduce9_add(gv, a.g_screen + (size_t)s_id[j] * 9, lane);
+            if (!__any_sync(0xffffffffu, e[0] || e[1] || e[2] || e[3])) continue;
+            const float4 C1 = S.s3[j], C2 = S.s4[j];
+            const float2 o2 = f2(C2.z, C2.w);
+            float2 X0, X1, X2, X3, X4, X5, X6, X7, X8;
+            bool contrib = false;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                BwdPair &q = P[r];
+                const float2 G = f2(__expf(pw[r].x), __expf(pw[r].y));
+                const float2 oG = __fmul2_rn(o2, G);
+                const float al0 = fminf(kAlphaMax, oG.x), al1 = fminf(kAlphaMax, oG.y);
+                const bool c0 = e[2 * r] && al0 >= kAlphaMin, c1 = e[2 * r + 1] && al1 >= kAlphaMin;
+                contrib = contrib || c0 || c1;
+                const float2 na = f2(c0 ? -al0 : 0.f, c1 ? -al1 : 0.f);
+                const float2 om = __fadd2_rn(one, na);  // 1 - alpha (1 where not composited)
+                const float2 inv = f2(c0 ? __fdividef(1.f, om.x) : 1.f, c1 ? __fdividef(1.f, om.y) : 1.f);
+                q.T = __fmul2_rn(q.T, inv);
+                const float2 nw = __fmul2_rn(na, q.T);  // -alpha T
+                const float2 S1 = __ffma2_rn(q.g0, f2(C1.x, C1.y),
+                                             __ffma2_rn(q.g1, f2(C1.z, C1.w), __fmul2_rn(q.g2, f2(C2.x, C2.y))));
+                const float2 dal = __ffma2_rn(inv, q.nS2, __fmul2_rn(q.T, S1));
+                q.nS2 = __ffma2_rn(nw, S1, q.nS2);
+                // derivative through o G where the cap does not bind
+                const float2 Gm = f2(c0 && oG.x < kAlphaMax ? G.x : 0.f, c1 && oG.y < kAlphaMax ? G.y : 0.f);
+                const float2 dp = __fmul2_rn(dal, __fmul2_rn(o2, Gm));
+                const float2 vx = __ffma2_rn(f2(Q.z, Q.w), dy[r], __fmul2_rn(two, cadx));
+                const float2 vy = __ffma2_rn(two, __fmul2_rn(cc2, dy[r]), B);
+                const float2 dpvx = __fmul2_rn(dp, vx), dpvy = __fmul2_rn(dp, vy);
+                if (r == 0) {
+                    X0 = dpvx;
+                    X1 = dpvy;
+                    X2 = __fmul2_rn(dpvx, vx);
+                    X3 = __fmul2_rn(dpvx, vy);
+                    X4 = __fmul2_rn(dpvy, vy);
+                    X5 = __fmul2_rn(Gm, dal);
+                    X6 = __fmul2_rn(nw, q.g0);
+                    X7 = __fmul2_rn(nw, q.g1);
+                    X8 = __fmul2_rn(nw, q.g2);
+                } else {
+                    X0 = __fadd2_rn(X0, dpvx);
+                    X1 = __fadd2_rn(X1, dpvy);
+                    X2 = __ffma2_rn(dpvx, vx, X2);
+                    X3 = __ffma2_rn(dpvx, vy, X3);
+                    X4 = __ffma2_rn(dpvy, vy, X4);
+                    X5 = __ffma2_rn(Gm, dal, X5);
+                    X6 = __ffma2_rn(nw, q.g0, X6);
+                    X7 = __ffma2_rn(nw, q.g1, X7);
+                    X8 = __ffma2_rn(nw, q.g2, X8);
+                }
+            }
+            if (__ballot_sync(0xffffffffu, contrib)) {
+                const float gv[9] = {X0.x + X0.y, X1.x + X1.y, 0.5f * (X2.x + X2.y), X3.x + X3.y,
+                                     0.5f * (X4.x + X4.y), X5.x + X5.y, -(X6.x + X6.y), -(X7.x + X7.y),
+                                     -(X8.x + X8.y)};
+                warp_reduce9_add(gv, a.g_screen + (size_t)S.id[j] * 9, lane);
+            }
         }
     }
 }
 
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
     __shared__ uint32_t s_id[kBwdBatch];
-    __shared__ float4 s_m[kBwdBatch], s_c[kBwdBatch], s_rgb[kBwdBatch];
+    __shared__ float4 s_st[5][kBwdBatch];
     __shared__ int s_maxlast;
-    render_bwd_tile(a, blockIdx.x, 0, s_id, s_m, s_c, s_rgb, &s_maxlast);
+    const BwdStage S{s_id, s_st[0], s_st[1], s_st[2], s_st[3], s_st[4], &s_maxlast};
+    render_bwd_tile(a, blockIdx.x, 0, S);
 }
 
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent_kernel(BwdArgs a) {
     __shared__ uint32_t s_id[kBwdBatch];
-    __shared__ float4 s_m[kBwdBatch], s_c[kBwdBatch], s_rgb[kBwdBatch];
+    __shared__ float4 s_st[5][kBwdBatch];
     __shared__ int s_maxlast;
     __shared__ uint32_t s_next;
+    const BwdStage S{s_id, s_st[0], s_st[1], s_st[2], s_st[3], s_st[4], &s_maxlast};
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(a.queue, (uint32_t)a.tiles_per_fetch);
         __syncthreads();
@@ -216,8 +279,7 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent_kernel(BwdA
         __syncthreads();
         if (t0 >= a.ts.total_tiles) break;
         const uint32_t t1 = min(t0 + (uint32_t)a.tiles_per_fetch, a.ts.total_tiles);
-        for (uint32_t t = t0; t < t1; ++t)
-            render_bwd_tile(a, t, camera_of(a.ts, t), s_id, s_m, s_c, s_rgb, &s_maxlast);
+        for (uint32_t t = t0; t < t1; ++t) render_bwd_tile(a, t, camera_of(a.ts, t), S);
     }
 }
 
