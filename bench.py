@@ -383,9 +383,9 @@ def kernel_work(P, n, n_eval):
 # scaled to a launch of this frame by its units; valid for the kernels as
 # captured (kernel -> (unit, bytes per unit)).
 TRAFFIC_PER_UNIT = {
-    "render_kernel": ("eval", (14.689024e6 + 2.035968e6) / 398728138),
-    "tile_sort_pass": ("pair", (167.909888e6 + 139.132160e6) / 20633099),
-    "tile_sort_pass_values": ("pair", (166.251264e6 + 42.776320e6) / 20633099),
+    "render_kernel": ("eval", (12.206848e6 + 1.605376e6) / 398728138),
+    "tile_sort_pass": ("pair", (166.167808e6 + 118.349568e6) / 20633099),
+    "tile_sort_pass_values": ("pair", (165.426688e6 + 30.919168e6) / 20633099),
     "emit_warp_kernel": ("pair", (54.315520e6 + 117.350400e6) / 20633099),
     "tile_count_kernel": ("pair", (82.578432e6 + 1.667840e6) / 20633099),
 }
@@ -456,8 +456,10 @@ def _time_ms(fn, steps, warmup, stream):
 
 
 def run_c3(args, dev):
-    """Zoom sweep: 3M Gaussians at 2560x1440, 30 views from distance 40 to 2;
-    tile pairs and forward FPS per view for QuadBox and the 3-sigma AABB."""
+    """Zoom sweep (Fig. 1 analogue): 3M Gaussians at 2560x1440, 30 views from
+    distance 40 to 2; tile pairs and forward FPS per view for every binning
+    mode on the same kernels (QuadBox and the 3-sigma AABB, plus AdR,
+    QuadBox without QPass, DualBox and the unclamped QuadBox)."""
     import numpy as np
     import torch
 
@@ -471,17 +473,20 @@ def run_c3(args, dev):
     stream = torch.cuda.current_stream(dev)
     frames = {}
     views = []
+    modes = ("quadbox", "aabb3s", "adr", "quadbox_naive", "dualbox", "quadbox+noclamp")
     for k, cam in enumerate(cams):
         d = float(-cam["viewmat"][2][3]) if "viewmat" in cam else None
         row = {"view": k, "distance": round(abs(d), 3) if d is not None else None}
         cs = R.camera_struct(cam)
-        for mode in ("quadbox", "aabb3s"):
+        for mode in modes:
+            # the two headline modes keep their own frames; the others share one
+            slot = mode if mode in ("quadbox", "aabb3s") else "other"
             try:
-                _, fr = R.forward(sd, cam, mode, frame=frames.get(mode))
+                _, fr = R.forward(sd, cam, mode, frame=frames.get(slot))
             except N.QbCapacityError:
                 row[mode] = {"pairs": None, "note": "over 2^30 pairs"}
                 continue
-            frames[mode] = fr
+            frames[slot] = fr
             pairs = fr.n_pairs
             img = torch.empty((3, cam["height"], cam["width"]), device=dev)
 
@@ -498,13 +503,15 @@ def run_c3(args, dev):
             row["speedup"] = round(row["aabb3s"]["fwd_ms"] / row["quadbox"]["fwd_ms"], 3)
         views.append(row)
     return {"workload": "3M Gaussians (ball of radius 10 at the origin), 2560x1440, SH3, 30 views on -z from "
-                        "distance 40 to 2 (geometric)", "views": views}
+                        "distance 40 to 2 (geometric); every binning mode on the same kernels", "views": views}
 
 
 def run_modes(args, dev):
     """The paper's ablation (Table 3) on C2: pairs per frame and forward time
-    of every binning mode on the same kernels (DualBox is not conservative:
-    its image differs by design)."""
+    of every binning mode on the same kernels, and each mode's image against
+    the clamped QuadBox image (the conservative modes must match it bit for
+    bit; DualBox is not conservative and the unclamped boxes reach beyond the
+    3-sigma rectangle, so those two differ by design)."""
     import numpy as np
     import torch
 
@@ -516,8 +523,10 @@ def run_modes(args, dev):
     s, cs = R.scene_struct(sd), R.camera_struct(cam)
     stream = torch.cuda.current_stream(dev)
     img = torch.empty((3, cam["height"], cam["width"]), device=dev)
-    out = {"workload": "C2 (1M Gaussians, 1920x1080, SH3), forward per binning mode, same kernels"}
-    for mode in ("aabb3s", "adr", "quadbox_naive", "quadbox", "dualbox"):
+    out = {"workload": "C2 (1M Gaussians, 1920x1080, SH3), forward per binning mode, same kernels; image delta "
+                       "against the clamped QuadBox image"}
+    ref = None
+    for mode in ("quadbox", "aabb3s", "adr", "quadbox_naive", "dualbox", "quadbox+noclamp", "adr+noclamp"):
         _, fr = R.forward(sd, cam, mode)
         pairs = fr.n_pairs
 
@@ -528,7 +537,15 @@ def run_modes(args, dev):
             fr.render(None, img)
         ms = _time_ms(fwd, 10, 3, stream)
         fr.check()
-        out[mode] = {"pairs": pairs, "fwd_ms": round(ms, 4), "fps": round(1000.0 / ms, 1)}
+        row = {"pairs": pairs, "fwd_ms": round(ms, 4), "fps": round(1000.0 / ms, 1)}
+        if ref is None:
+            ref = img.clone()
+        else:
+            diff = (img - ref).abs()
+            row["image_vs_quadbox"] = {"identical": bool(torch.equal(img, ref)),
+                                       "max_abs": round(float(diff.max().item()), 6),
+                                       "pixels_differing": int((diff.amax(dim=0) > 0).sum().item())}
+        out[mode] = row
         del fr
     return out
 
