@@ -367,8 +367,7 @@ def kernel_work(P, n, n_eval):
         "preprocess_kernel": ("hbm", n * PREPROCESS_BYTES),
         "sort_hist_kernel": ("hbm", n * 4),              # the depth keys once
         "onesweep_kernel": ("hbm", n * 16),              # a depth-sort pass: key + value read and written
-        "scan_reduce_kernel": ("hbm", n * 8),
-        "scan_down_kernel": ("hbm", n * 12),
+        "scan_onepass_kernel": ("hbm", n * 12),        # depth order read, counts gathered, offsets written
         "emit_warp_kernel": ("hbm", P * 8 + n * 28),     # pairs written; depth order, offset, count, segments
         "tile_count_kernel": ("hbm", P * 4),             # the tile ids once
         "tile_sort_pass": ("hbm", P * 16),               # key + value read and written

@@ -84,7 +84,7 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     L.chunk_start = take(4 * (n_chunks + 1));
     L.chunk_cnt = take(4 * n_chunks * (size_t)tiles);
     L.chunk_part = take(4 * (size_t)kChunkSegs * tiles);
-    L.chunk_total = take(4 * (size_t)tiles);
+    L.chunk_total = take(4 * ((size_t)tiles + 1));  // + the tile histogram's block counter
     L.tile_diff = take(4 * (size_t)(tx + 1) * (ty + 1));
     L.tile_single = take(4 * (size_t)tiles);
     L.tfinal = take(4 * (size_t)W * H);
@@ -388,7 +388,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         perm = frame->depth_in_alt ? dv1 : dv0;
     }
     QB_CUDA(launch_scan(at<uint32_t>(frame, L.counts), perm, frame->n, at<uint32_t>(frame, L.offsets),
-                        at<uint64_t>(frame, L.scan_part), d_np, s));
+                        at<uint64_t>(frame, L.scan_part), d_np, err, s));
     if (eff == QB_SORT_DEPTH_FIRST && fused) {
         // per-tile counts -> ranges and the tile sort's bucket offsets
         const int tile_bits = frame->key_bits - kDepthBits;
@@ -526,11 +526,9 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
             // pass's bucket offsets
             const uint32_t *src = at<uint32_t>(frame, passes > 0 && pass_writes_a(passes, 0) ? L.keys1 : L.keys0);
             uint32_t *counts = at<uint32_t>(frame, L.chunk_total);
-            const uint32_t zero_off[1] = {0u};
-            QB_CUDA(launch_tile_count(src, n_max, n_dev, ntiles, counts, s));
-            QB_CUDA(launch_tile_prep(nullptr, nullptr, counts, frame_tileset(frame), zero_off, zero_off,
-                                     at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
-                                     sort_hist_stride(), rb, tile_bits, frame->pair_capacity, s));
+            QB_CUDA(launch_tile_count(src, n_max, n_dev, ntiles, counts, at<uint2>(frame, L.ranges),
+                                      sort_hist_table(at<void>(frame, L.sort_scratch)), sort_hist_stride(), rb,
+                                      tile_bits, s));
         }
         if (passes > 0)
             QB_CUDA(tile_sort_passes(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),

@@ -335,7 +335,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
                                 err, s, &passes));
         const uint32_t *perm = (passes & 1) ? dv1 : dv0;
         QB_BCUDA(launch_scan(a.counts, perm, nrec, bat<uint32_t>(b, L.offsets), bat<uint64_t>(b, L.scan_part),
-                             npairs + gi, s));
+                             npairs + gi, err, s));
         // ---- per-tile counts -> ranges and the tile sort's bucket offsets ----
         const int tpasses = v.tile_bits > 0 ? (v.tile_bits + t.sort_digit_bits - 1) / t.sort_digit_bits : 0;
         uint2 *ranges = bat<uint2>(b, L.ranges) + v.tile0;

@@ -50,65 +50,129 @@ __device__ __forceinline__ uint32_t count_at(const uint32_t *counts, const uint3
     return perm ? counts[perm[j]] : counts[j];
 }
 
-__global__ void __launch_bounds__(kScanBlock) scan_reduce_kernel(const uint32_t *counts, const uint32_t *perm, int n,
-                                                                 uint64_t *partials) {
-    const size_t base = (size_t)blockIdx.x * kScanChunk;
-    uint64_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        size_t idx = base + (size_t)k * kScanBlock + threadIdx.x;
-        if (idx < (size_t)n) s += count_at(counts, perm, idx);
-    }
-    uint64_t total;
-    block_incl_scan<uint64_t>(s, &total);
-    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+// K2 in one pass: block b (taken in launch order from a counter, so every
+// earlier block is already running) scans its kScanChunk counts, publishes
+// its sum, looks back over the earlier blocks' published words for its
+// running total (decoupled look-back) and writes its offsets.  Status word of
+// a block: flag (bit 63: sum of the block, bit 62: total through the block)
+// and a 62-bit count.  The last block writes P.
+constexpr uint64_t kScanAgg = 1ull << 63, kScanIncl = 1ull << 62, kScanCount = kScanIncl - 1;
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void __launch_bounds__(1024) scan_partials_kernel(uint64_t *partials, int nb, uint64_t *n_pairs) {
-    uint64_t running = 0;
-    for (int base = 0; base < nb; base += 1024) {
-        int idx = base + threadIdx.x;
-        uint64_t v = idx < nb ? partials[idx] : 0;
-        uint64_t total;
-        uint64_t incl = block_incl_scan<uint64_t>(v, &total);
-        if (idx < nb) partials[idx] = running + incl - v;
-        running += total;
-    }
-    if (threadIdx.x == 0) *n_pairs = running;
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Each thread scans kScanItems consecutive counts (in emission order).
-__global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const uint32_t *counts, const uint32_t *perm, int n,
-                                                               const uint64_t *partials, uint32_t *offsets) {
-    const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanItems;
+__global__ void __launch_bounds__(kScanBlock) scan_onepass_kernel(const uint32_t *__restrict__ counts,
+                                                                  const uint32_t *__restrict__ perm, int n,
+                                                                  uint32_t *__restrict__ offsets, uint64_t *status,
+                                                                  uint32_t *counter, uint64_t *n_pairs, uint32_t *err) {
+    __shared__ uint32_t s_block;
+    __shared__ uint64_t s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) s_block = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t b = s_block;
+    const int nb = (n + kScanChunk - 1) / kScanChunk;
+    // each thread scans kScanItems consecutive counts (in emission order)
+    const size_t base = (size_t)b * kScanChunk + (size_t)tid * kScanItems;
     uint32_t c[kScanItems];
-    uint64_t s = 0;
+    uint64_t sum = 0;
+    if (base + kScanItems <= (size_t)n && perm) {
+        uint32_t g[kScanItems];
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        size_t idx = base + k;
-        c[k] = idx < (size_t)n ? count_at(counts, perm, idx) : 0u;
-        s += c[k];
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 v = reinterpret_cast<const uint4 *>(perm + base)[q];
+            g[4 * q] = v.x, g[4 * q + 1] = v.y, g[4 * q + 2] = v.z, g[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) c[k] = counts[g[k]];
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) c[k] = base + k < (size_t)n ? count_at(counts, perm, base + k) : 0u;
     }
-    uint64_t total;
-    uint64_t incl = block_incl_scan<uint64_t>(s, &total);
-    uint64_t run = partials[blockIdx.x] + incl - s;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        size_t idx = base + k;
-        if (idx < (size_t)n) offsets[idx] = (uint32_t)run;  // P <= 2^30 is checked before use
-        run += c[k];
+    for (int k = 0; k < kScanItems; ++k) sum += c[k];
+    uint64_t total;
+    const uint64_t incl = block_incl_scan<uint64_t>(sum, &total);
+    // publish, then look back (warp 0, 32 earlier blocks per step)
+    if (tid == 0) st_relaxed_u64(status + b, (b == 0 ? kScanIncl : kScanAgg) | total);
+    if (tid < 32) {
+        // The words of blocks t, t - 1, ..., t - 31 are read together; the
+        // sums of the lanes before the first word not yet published are
+        // added, up to and including the first inclusive word, which ends the
+        // walk.  (Before block 0 reads as an inclusive zero.)
+        uint64_t acc = 0;
+        int64_t t = (int64_t)b - 1;
+        int spins = 0;
+        while (t >= 0) {
+            const int64_t mine = t - lane;
+            const uint64_t w = mine >= 0 ? ld_relaxed_u64(status + mine) : kScanIncl;
+            const uint32_t ready = __ballot_sync(0xffffffffu, (w & (kScanAgg | kScanIncl)) != 0);
+            const uint32_t inclm = __ballot_sync(0xffffffffu, (w & kScanIncl) != 0);
+            const int first_unready = ready == 0xffffffffu ? 32 : __ffs(~ready) - 1;
+            const int first_incl = inclm ? __ffs(inclm) - 1 : 32;
+            const bool ends = first_incl < first_unready;
+            const int used = ends ? first_incl + 1 : first_unready;
+            uint64_t v = lane < used ? (w & kScanCount) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc += v;
+            if (ends) break;
+            if (used > 0) {
+                t -= used;
+                continue;
+            }
+            // the nearest earlier block has not published yet
+            if (++spins > kSpinLimit) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (lane == 0) {
+            if (b > 0) st_relaxed_u64(status + b, kScanIncl | ((acc + total) & kScanCount));
+            s_prefix = acc;
+            if ((int)b == nb - 1) *n_pairs = acc + total;
+        }
+    }
+    __syncthreads();
+    uint64_t run = s_prefix + incl - sum;
+    if (base + kScanItems <= (size_t)n) {
+        uint32_t o[kScanItems];
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            o[k] = (uint32_t)run;  // P <= 2^30 is checked before use
+            run += c[k];
+        }
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q)
+            reinterpret_cast<uint4 *>(offsets + base)[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < (size_t)n) offsets[base + k] = (uint32_t)run;
+            run += c[k];
+        }
     }
 }
 
+// status words for the blocks, then the block counter
 size_t scan_partials_count(int n) { return (size_t)((n + kScanChunk - 1) / kScanChunk) + 1; }
 
 cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uint32_t *offsets, uint64_t *partials,
-                        uint64_t *n_pairs, cudaStream_t s) {
+                        uint64_t *n_pairs, uint32_t *err, cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(n_pairs, 0, sizeof(uint64_t), s);
-    int nb = (n + kScanChunk - 1) / kScanChunk;
-    note_launch("scan_reduce_kernel", s), scan_reduce_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials);
-    note_launch("scan_partials_kernel", s), scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nb, n_pairs);
-    note_launch("scan_down_kernel", s), scan_down_kernel<<<nb, kScanBlock, 0, s>>>(counts, perm, n, partials, offsets);
+    const int nb = (n + kScanChunk - 1) / kScanChunk;
+    cudaError_t e = cudaMemsetAsync(partials, 0, ((size_t)nb + 1) * sizeof(uint64_t), s);
+    if (e != cudaSuccess) return e;
+    note_launch("scan_onepass_kernel", s), scan_onepass_kernel<<<nb, kScanBlock, 0, s>>>(
+        counts, perm, n, offsets, partials, reinterpret_cast<uint32_t *>(partials + nb), n_pairs, err);
     return cudaGetLastError();
 }
 
@@ -915,9 +979,67 @@ cudaError_t launch_expand_ranges(const uint2 *ranges, int ntiles, uint32_t *out,
 
 // Per-tile pair counts from the emitted tile ids: a shared-memory histogram
 // per block, merged into counts (zeroed by the caller) with global atomics.
+// From the per-tile counts (s_counts, in shared memory; all zero when the
+// pairs exceed the capacity): the ranges, and for every pass of the tile
+// sort the exclusive bucket offsets of its digit, run by one block.  A
+// digit's bucket sums the counts of the tiles with that digit, read in the
+// tile order of the shared counts (no atomics).
+__device__ __forceinline__ void prep_from_counts(const uint32_t *s_counts, int ntiles, uint2 *ranges, uint32_t *hist,
+                                                 int hist_stride, const PassGeo &g) {
+    const int per = (ntiles + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int t0 = (int)threadIdx.x * per, t1 = min(ntiles, t0 + per);
+    uint32_t local = 0;
+#pragma unroll 8
+    for (int t = t0; t < t1; ++t) local += s_counts[t];
+    uint32_t total;
+    uint32_t run = block_incl_scan<uint32_t>(local, &total) - local;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = s_counts[t];
+        ranges[t] = c ? make_uint2(run, run + c) : make_uint2(0u, 0u);  // [0,0) for an empty tile
+        run += c;
+    }
+    constexpr int kMaxPer = (1 << kMaxDigitBits) / 512;
+    for (int p = 0; p < g.passes; ++p) {
+        const int Rp = 1 << g.bits[p], sh = g.shift[p];
+        const int per_d = (Rp + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int d0 = (int)threadIdx.x * per_d;
+        uint32_t dsum[kMaxPer > 0 ? kMaxPer : 1];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < (kMaxPer > 0 ? kMaxPer : 1); ++k) {
+            dsum[k] = 0u;
+            const int d = d0 + k;
+            if (k >= per_d || d >= Rp) continue;
+            // tiles whose digit p is d: runs of 2^sh consecutive ids, every Rp 2^sh
+            for (int t = d << sh; t < ntiles; t += Rp << sh) {
+                const int te = min(ntiles, t + (1 << sh));
+#pragma unroll 8
+                for (int u = t; u < te; ++u) dsum[k] += s_counts[u];
+            }
+            sum += dsum[k];
+        }
+        uint32_t tot;
+        uint32_t r = block_incl_scan<uint32_t>(sum, &tot) - sum;
+#pragma unroll
+        for (int k = 0; k < (kMaxPer > 0 ? kMaxPer : 1); ++k) {
+            const int d = d0 + k;
+            if (k >= per_d || d >= Rp) continue;
+            hist[p * hist_stride + d] = r;
+            r += dsum[k];
+        }
+    }
+}
+
+// Shared-memory histogram of the emitted tile ids, added into counts.  With
+// prep, the last block to finish (a counter at counts[ntiles], zero at
+// launch) turns the totals into the ranges and the tile sort's bucket offsets
+// (prep_from_counts), so no separate launch waits for the histogram.
 __global__ void __launch_bounds__(512) tile_count_kernel(const uint32_t *__restrict__ keys, uint64_t n_max,
-                                                         const uint64_t *n_dev, uint32_t ntiles, uint32_t *counts) {
+                                                         const uint64_t *n_dev, uint32_t ntiles, uint32_t *counts,
+                                                         bool prep, uint2 *ranges, uint32_t *hist, int hist_stride,
+                                                         PassGeo g) {
     extern __shared__ uint32_t s_hist[];
+    __shared__ bool s_last;
     for (uint32_t t = threadIdx.x; t < ntiles; t += blockDim.x) s_hist[t] = 0u;
     __syncthreads();
     const uint64_t n = device_count(n_dev, n_max);
@@ -939,12 +1061,38 @@ __global__ void __launch_bounds__(512) tile_count_kernel(const uint32_t *__restr
         const uint32_t v = s_hist[t];
         if (v) atomicAdd(&counts[t], v);
     }
+    if (!prep) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&counts[ntiles], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // (more pairs than the buffers hold: device_count gave 0 and every count is 0)
+    // eight independent loads in flight per thread
+    for (uint32_t b0 = 0; b0 < ntiles; b0 += 8 * blockDim.x) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t t = b0 + k * blockDim.x + threadIdx.x;
+            v[k] = t < ntiles ? __ldcg(counts + t) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t t = b0 + k * blockDim.x + threadIdx.x;
+            if (t < ntiles) s_hist[t] = v[k];
+        }
+    }
+    __syncthreads();
+    prep_from_counts(s_hist, (int)ntiles, ranges, hist, hist_stride, g);
 }
 
 cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64_t *n_dev, int ntiles,
-                              uint32_t *counts, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * (size_t)ntiles, s);
-    if (e != cudaSuccess || n_max == 0 || ntiles == 0) return e;
+                              uint32_t *counts, uint2 *ranges, uint32_t *hist, int hist_stride, int digit_bits,
+                              int tile_bits, cudaStream_t s) {
+    // the counts and the finished-block counter after them
+    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * ((size_t)ntiles + 1), s);
+    if (e != cudaSuccess || ntiles == 0) return e;
     const size_t smem = 4 * (size_t)ntiles;
     static size_t set = 0;
     if (smem > set) {
@@ -959,7 +1107,9 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
     uint64_t blocks = (n_max / 4 + 511) / 512;
     if (blocks > (uint64_t)sms * 2) blocks = (uint64_t)sms * 2;
     if (blocks == 0) blocks = 1;
-    note_launch("tile_count_kernel", s), tile_count_kernel<<<(unsigned)blocks, 512, smem, s>>>(keys, n_max, n_dev, (uint32_t)ntiles, counts);
+    const PassGeo g = pass_geo(tile_bits, digit_bits);
+    note_launch("tile_count_kernel", s), tile_count_kernel<<<(unsigned)blocks, 512, smem, s>>>(
+        keys, n_max, n_dev, (uint32_t)ntiles, counts, ranges != nullptr, ranges, hist, hist_stride, g);
     return cudaGetLastError();
 }
 

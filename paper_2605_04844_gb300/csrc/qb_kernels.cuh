@@ -159,8 +159,11 @@ struct PreBwdArgs {
 };
 
 cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s);
+// partials: scan_partials_count(n) words of scratch (block status words and
+// the block counter), cleared by the launch; a look-back that waits too long
+// raises kErrTimeout in *err.
 cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uint32_t *offsets, uint64_t *partials,
-                        uint64_t *n_pairs, cudaStream_t s);
+                        uint64_t *n_pairs, uint32_t *err, cudaStream_t s);
 size_t scan_partials_count(int n);
 template <typename KeyT>
 cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s);
@@ -181,10 +184,14 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
 cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint32_t *counts, const TileSet &ts,
                              const uint32_t *diff_off, const uint32_t *single_off, uint2 *ranges, uint32_t *hist,
                              int hist_stride, int digit_bits, int tile_bits, uint64_t capacity, cudaStream_t s);
-// Per-tile counts of n tile ids (counts zeroed here); ntiles <= kTileCountMax.
+// Per-tile counts of n tile ids into counts[0, ntiles) (counts and the
+// block counter at counts[ntiles] zeroed here); ntiles <= kTileCountMax.
+// With ranges non-null the last block also writes the ranges and every
+// tile-sort pass's exclusive bucket offsets (hist, stride hist_stride).
 constexpr int kTileCountMax = 24576;
 cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64_t *n_dev, int ntiles,
-                              uint32_t *counts, cudaStream_t s);
+                              uint32_t *counts, uint2 *ranges, uint32_t *hist, int hist_stride, int digit_bits,
+                              int tile_bits, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs &a, int batch, cudaStream_t s);
 cudaError_t launch_l1_grad(const float *img, const float *target, float *dL, uint64_t n, float scale, double *loss,
                            cudaStream_t s);
