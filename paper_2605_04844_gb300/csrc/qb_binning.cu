@@ -979,61 +979,74 @@ cudaError_t launch_expand_ranges(const uint2 *ranges, int ntiles, uint32_t *out,
 
 // Per-tile pair counts from the emitted tile ids: a shared-memory histogram
 // per block, merged into counts (zeroed by the caller) with global atomics.
-// From the per-tile counts (s_counts, in shared memory; all zero when the
-// pairs exceed the capacity): the ranges, and for every pass of the tile
-// sort the exclusive bucket offsets of its digit, run by one block.  A
-// digit's bucket sums the counts of the tiles with that digit, read in the
-// tile order of the shared counts (no atomics).
-__device__ __forceinline__ void prep_from_counts(const uint32_t *s_counts, int ntiles, uint2 *ranges, uint32_t *hist,
-                                                 int hist_stride, const PassGeo &g) {
+// From the per-tile counts, run by one block: the ranges, and for every pass
+// of the tile sort the exclusive bucket offsets of its digit.  s[0, ntiles)
+// holds the counts (all zero when the pairs exceed the capacity) and becomes
+// the exclusive offsets, s[ntiles] the total (prep_ranges); s_dsum has room
+// for 2^kMaxDigitBits digit sums.
+__device__ __forceinline__ void prep_ranges(uint32_t *s, int ntiles, uint2 *ranges) {
+    // each thread turns a contiguous chunk into offsets, then the ranges
+    // leave in tile order (coalesced)
     const int per = (ntiles + (int)blockDim.x - 1) / (int)blockDim.x;
     const int t0 = (int)threadIdx.x * per, t1 = min(ntiles, t0 + per);
     uint32_t local = 0;
 #pragma unroll 8
-    for (int t = t0; t < t1; ++t) local += s_counts[t];
+    for (int t = t0; t < t1; ++t) local += s[t];
     uint32_t total;
     uint32_t run = block_incl_scan<uint32_t>(local, &total) - local;
     for (int t = t0; t < t1; ++t) {
-        const uint32_t c = s_counts[t];
-        ranges[t] = c ? make_uint2(run, run + c) : make_uint2(0u, 0u);  // [0,0) for an empty tile
+        const uint32_t c = s[t];
+        s[t] = run;
         run += c;
     }
-    constexpr int kMaxPer = (1 << kMaxDigitBits) / 512;
+    if (threadIdx.x == 0) s[ntiles] = total;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t o0 = s[t], o1 = s[t + 1];
+        ranges[t] = o1 > o0 ? make_uint2(o0, o1) : make_uint2(0u, 0u);  // [0,0) for an empty tile
+    }
+}
+
+// After prep_ranges.  A digit d of pass p (width b, shift h) covers the runs
+// of 2^h consecutive tiles that start at u 2^(b+h) + d 2^h; each run's sum is
+// a difference of two offsets.  The runs are spread over the block's threads
+// (consecutive runs, consecutive digits: no conflicting shared atomics).
+__device__ __forceinline__ void prep_digits(const uint32_t *s, uint32_t *s_dsum, int ntiles, uint32_t *hist,
+                                            int hist_stride, const PassGeo &g) {
     for (int p = 0; p < g.passes; ++p) {
         const int Rp = 1 << g.bits[p], sh = g.shift[p];
-        const int per_d = (Rp + (int)blockDim.x - 1) / (int)blockDim.x;
-        const int d0 = (int)threadIdx.x * per_d;
-        uint32_t dsum[kMaxPer > 0 ? kMaxPer : 1];
-        uint32_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < (kMaxPer > 0 ? kMaxPer : 1); ++k) {
-            dsum[k] = 0u;
-            const int d = d0 + k;
-            if (k >= per_d || d >= Rp) continue;
-            // tiles whose digit p is d: runs of 2^sh consecutive ids, every Rp 2^sh
-            for (int t = d << sh; t < ntiles; t += Rp << sh) {
-                const int te = min(ntiles, t + (1 << sh));
-#pragma unroll 8
-                for (int u = t; u < te; ++u) dsum[k] += s_counts[u];
-            }
-            sum += dsum[k];
+        const int period = Rp << sh;
+        const int runs = Rp * ((ntiles + period - 1) / period);
+        for (int d = threadIdx.x; d < Rp; d += blockDim.x) s_dsum[d] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < runs; i += blockDim.x) {
+            const int d = i & (Rp - 1), u = i >> g.bits[p];
+            const int a = u * period + (d << sh);
+            if (a >= ntiles) continue;
+            const int e = min(ntiles, a + (1 << sh));
+            const uint32_t v = s[e] - s[a];
+            if (v) atomicAdd(&s_dsum[d], v);
         }
+        __syncthreads();
+        // exclusive offsets over the digits, a contiguous chunk per thread
+        const int per_d = (Rp + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int d0 = (int)threadIdx.x * per_d, d1 = min(Rp, d0 + per_d);
+        uint32_t sum = 0;
+        for (int d = d0; d < d1; ++d) sum += s_dsum[d];
         uint32_t tot;
         uint32_t r = block_incl_scan<uint32_t>(sum, &tot) - sum;
-#pragma unroll
-        for (int k = 0; k < (kMaxPer > 0 ? kMaxPer : 1); ++k) {
-            const int d = d0 + k;
-            if (k >= per_d || d >= Rp) continue;
+        for (int d = d0; d < d1; ++d) {
             hist[p * hist_stride + d] = r;
-            r += dsum[k];
+            r += s_dsum[d];
         }
+        __syncthreads();
     }
 }
 
 // Shared-memory histogram of the emitted tile ids, added into counts.  With
 // prep, the last block to finish (a counter at counts[ntiles], zero at
 // launch) turns the totals into the ranges and the tile sort's bucket offsets
-// (prep_from_counts), so no separate launch waits for the histogram.
+// (prep_ranges, prep_digits), so no separate launch waits for the histogram.
 __global__ void __launch_bounds__(512) tile_count_kernel(const uint32_t *__restrict__ keys, uint64_t n_max,
                                                          const uint64_t *n_dev, uint32_t ntiles, uint32_t *counts,
                                                          bool prep, uint2 *ranges, uint32_t *hist, int hist_stride,
@@ -1084,7 +1097,8 @@ __global__ void __launch_bounds__(512) tile_count_kernel(const uint32_t *__restr
         }
     }
     __syncthreads();
-    prep_from_counts(s_hist, (int)ntiles, ranges, hist, hist_stride, g);
+    prep_ranges(s_hist, (int)ntiles, ranges);
+    prep_digits(s_hist, s_hist + ntiles + 1, (int)ntiles, hist, hist_stride, g);
 }
 
 cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64_t *n_dev, int ntiles,
@@ -1093,7 +1107,8 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
     // the counts and the finished-block counter after them
     cudaError_t e = cudaMemsetAsync(counts, 0, 4 * ((size_t)ntiles + 1), s);
     if (e != cudaSuccess || ntiles == 0) return e;
-    const size_t smem = 4 * (size_t)ntiles;
+    // the histogram; for the last block's prep also the total and the digit sums
+    const size_t smem = 4 * ((size_t)ntiles + 1 + ((size_t)1 << kMaxDigitBits));
     static size_t set = 0;
     if (smem > set) {
         if ((e = cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
