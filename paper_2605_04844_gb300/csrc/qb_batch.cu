@@ -2,9 +2,13 @@
 // qb_render_batch).  The cameras are taken in groups; for a group every stage
 // of the rasteriser runs once over all of its (camera, Gaussian) records:
 // preprocess (one grid row per camera), depth order of the records, scan,
-// per-tile counts, QPass emit with tile ids global over the group, tile sort,
-// and a persistent render that takes tiles of any of the group's cameras from
-// one work queue.  Nothing synchronises the host, so a whole call can be
+// QPass emit with tile ids global over the group, a stable sort on those ids
+// (per-pass digit histograms, every pass writing keys), the ranges from the
+// sorted ids, and a persistent render that takes tiles of any of the group's
+// cameras from one work queue.  (The group's ~10^5 tiles are too many for the
+// shared-memory tile histogram of the single-frame path, and counting them
+// from the preprocess by atomics on difference arrays cost more than the
+// sort's own histograms and a ranges pass.)  Nothing synchronises the host, so a whole call can be
 // captured in a CUDA graph.  The records, the sorted values, the ranges and
 // the per-pixel state of every camera stay in the workspace for
 // qb_render_batch_bwd.
@@ -60,7 +64,7 @@ struct BLayout {
     size_t tfinal, ncontrib, neval;                   // [total pixels]
     size_t keysA, keysB, valsT;                       // [cap] group scratch
     size_t offsets, segs, scan_part, dk0, dk1, dv0, dv1;  // [group * n]
-    size_t dsort, sort, diff, single, gscreen, queue, state;
+    size_t dsort, sort, gscreen, queue, state;
     size_t total;
 };
 
@@ -68,17 +72,9 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
     if (n < 0 || group < 1 || group > QB_GROUP_MAX || cap > (1ull << 30)) return false;
     const int n_groups = (n_cams + group - 1) / group;
     const size_t recs = (size_t)n_cams * n, grecs = (size_t)group * n;
-    size_t max_diff = 0, max_single = 0;
     int max_tile_bits = 1;
     for (int g0 = 0; g0 < n_cams; g0 += group) {
         const int g1 = g0 + group < n_cams ? g0 + group : n_cams;
-        size_t d = 0, sg = 0;
-        for (int k = g0; k < g1; ++k) {
-            d += (size_t)(g.tx[k] + 1) * (g.ty[k] + 1);
-            sg += (size_t)g.tx[k] * g.ty[k];
-        }
-        max_diff = d > max_diff ? d : max_diff;
-        max_single = sg > max_single ? sg : max_single;
         const int tb = bits_for(g.tile_base[g1] - g.tile_base[g0]);
         max_tile_bits = tb > max_tile_bits ? tb : max_tile_bits;
     }
@@ -119,8 +115,6 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
     }
     L.dsort = take(db);
     L.sort = take(sb);
-    L.diff = take(4 * max_diff);
-    L.single = take(4 * max_single);
     L.gscreen = take(72 * grecs);
     L.queue = take(256);
     L.state = take(8 * (size_t)n_groups + 256);
@@ -161,8 +155,6 @@ struct GroupView {
     int tile_bits;
     CamSet cs;
     TileSet ts;
-    uint32_t diff_off[kMaxGroupCams], single_off[kMaxGroupCams];
-    size_t diff_ints, single_ints;
 };
 
 void group_view(const qb_batch *b, const Geo &g, const qb_camera *cams, int gi, GroupView &v) {
@@ -177,7 +169,6 @@ void group_view(const qb_batch *b, const Geo &g, const qb_camera *cams, int gi, 
     v.cs.n_cams = v.ncam;
     v.ts.n_cams = v.ncam;
     v.ts.total_tiles = v.ntiles;
-    uint32_t d = 0, sg = 0;
     for (int c = 0; c < v.ncam; ++c) {
         const int k = v.k0 + c;
         if (cams) v.cs.cam[c] = cam_dev(cams[k]);
@@ -187,13 +178,7 @@ void group_view(const qb_batch *b, const Geo &g, const qb_camera *cams, int gi, 
         v.ts.cam[c].tiles_y = g.ty[k];
         v.ts.cam[c].tile_base = (uint32_t)(g.tile_base[k] - v.tile0);
         v.ts.cam[c].pix_base = g.pix_base[k];
-        v.diff_off[c] = d;
-        v.single_off[c] = sg;
-        d += (uint32_t)((g.tx[k] + 1) * (g.ty[k] + 1));
-        sg += (uint32_t)(g.tx[k] * g.ty[k]);
     }
-    v.diff_ints = d;
-    v.single_ints = sg;
 }
 
 qb_status check_batch(const qb_batch *b, Geo &g, BLayout &L) {
@@ -292,9 +277,6 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         group_view(b, geo, cams, gi, v);
         const int nrec = v.ncam * n;
         // ---- preprocess over (camera, Gaussian) records ----
-        int *diff = bat<int>(b, L.diff), *single = bat<int>(b, L.single);
-        QB_BCUDA(cudaMemsetAsync(diff, 0, 4 * v.diff_ints, s));
-        QB_BCUDA(cudaMemsetAsync(single, 0, 4 * v.single_ints, s));
         PreArgs a;
         std::memset(&a, 0, sizeof(a));
         a.n = n;
@@ -316,13 +298,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         a.r3 = bat<float>(b, L.r3) + v.rec0;
         a.meta = bat<int>(b, L.meta) + v.rec0;
         a.counts = bat<uint32_t>(b, L.counts) + v.rec0;
-        a.tile_diff = diff;
-        a.tile_single = single;
         a.segs = bat<uint4>(b, L.segs);
-        for (int c = 0; c < v.ncam; ++c) {
-            a.diff_off[c] = v.diff_off[c];
-            a.single_off[c] = v.single_off[c];
-        }
         uint32_t *dk0 = bat<uint32_t>(b, L.dk0), *dk1 = bat<uint32_t>(b, L.dk1);
         uint32_t *dv0 = bat<uint32_t>(b, L.dv0), *dv1 = bat<uint32_t>(b, L.dv1);
         a.depth_keys = dk0;  // the depth-order sort's keys, written by the preprocess
@@ -336,18 +312,18 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         const uint32_t *perm = (passes & 1) ? dv1 : dv0;
         QB_BCUDA(launch_scan(a.counts, perm, nrec, bat<uint32_t>(b, L.offsets), bat<uint64_t>(b, L.scan_part),
                              npairs + gi, err, s));
-        // ---- per-tile counts -> ranges and the tile sort's bucket offsets ----
-        const int tpasses = v.tile_bits > 0 ? (v.tile_bits + t.sort_digit_bits - 1) / t.sort_digit_bits : 0;
+        // ---- QPass emit of (group tile id, record) pairs in depth order,
+        // stable sort on the tile id (every pass writes keys and values), and
+        // the ranges from the sorted tile ids.  The emit writes the buffer
+        // pair from which the last pass lands in (keysA, this group's slot).
+        const PassGeo tg = pass_geo(v.tile_bits, t.sort_digit_bits);
+        const int tpasses = v.tile_bits > 0 ? tg.passes : 0;
         uint2 *ranges = bat<uint2>(b, L.ranges) + v.tile0;
-        QB_BCUDA(launch_tile_prep(diff, single, nullptr, v.ts, v.diff_off, v.single_off, ranges,
-                                  sort_hist_table(bat<void>(b, L.sort)), sort_hist_stride(), t.sort_digit_bits,
-                                  v.tile_bits, b->pair_capacity, s));
-        // ---- QPass emit fused with the tile sort's first pass; the sorted
-        // values end in this group's slot (buffer A = keysA + slot) ----
         uint32_t *slot = bat<uint32_t>(b, L.slots) + (size_t)gi * b->pair_capacity;
         uint32_t *valsT = bat<uint32_t>(b, L.valsT);
         uint32_t *keysA = bat<uint32_t>(b, L.keysA), *keysB = bat<uint32_t>(b, L.keysB);
         void *sort_scratch = bat<void>(b, L.sort);
+        const bool into_a = tpasses % 2 == 0;
         EmitArgs e;
         std::memset(&e, 0, sizeof(e));
         e.n = nrec;
@@ -360,6 +336,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         e.rgbd = a.rgbd;
         e.counts = a.counts;
         e.offsets = bat<uint32_t>(b, L.offsets);
+        e.vals = into_a ? slot : valsT;
         e.n_pairs = npairs + gi;
         e.n_pairs_host = UINT64_MAX;
         e.capacity = b->pair_capacity;
@@ -368,24 +345,14 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         e.err = err;
         e.ts = v.ts;
         e.segs = bat<uint4>(b, L.segs);
-        int first_pass = 0;
-        if (tpasses > 0 && base_mode != QB_BIN_QUADBOX_NAIVE) {
-            const bool to_a = pass_writes_a(tpasses, 0);
-            QB_BCUDA(sort_clear(sort_scratch, b->pair_capacity, t.sort_digit_bits, 0, 1, s));
-            QB_BCUDA(launch_emit_sweep(e, pass_geo(v.tile_bits, t.sort_digit_bits).bits[0], tpasses > 1,
-                                       to_a ? keysA : keysB, to_a ? slot : valsT,
-                                       sort_hist_table(sort_scratch),
-                                       sort_lookback(sort_scratch, b->pair_capacity, t.sort_digit_bits, 0),
-                                       sort_counter(sort_scratch, 0), s));
-            first_pass = 1;
-        } else {
-            const bool into_a = tpasses == 0 || !pass_writes_a(tpasses, 0);
-            e.vals = into_a ? slot : valsT;
-            QB_BCUDA(launch_emit<uint32_t>(e, into_a ? keysA : keysB, s));
+        QB_BCUDA(launch_emit<uint32_t>(e, into_a ? keysA : keysB, s));
+        if (tpasses > 0) {
+            int done = 0;
+            QB_BCUDA(sort_pairs(into_a ? keysA : keysB, into_a ? slot : valsT, into_a ? keysB : keysA,
+                                into_a ? valsT : slot, b->pair_capacity, npairs + gi, v.tile_bits, t.sort_digit_bits,
+                                sort_scratch, err, s, &done, false));
         }
-        if (tpasses > first_pass)
-            QB_BCUDA(tile_sort_passes(keysA, slot, keysB, valsT, b->pair_capacity, b->pair_capacity, npairs + gi,
-                                      v.tile_bits, first_pass, t.sort_digit_bits, sort_scratch, err, s));
+        QB_BCUDA(launch_ranges<uint32_t>(keysA, b->pair_capacity, npairs + gi, ranges, (int)v.ts.total_tiles, s));
         // ---- persistent render over the group's tiles ----
         QB_BCUDA(cudaMemsetAsync(bat<uint32_t>(b, L.queue), 0, 4, s));
         RenderArgs r;

@@ -553,14 +553,55 @@ __global__ void ranges_kernel(const KeyT *keys, uint64_t n_max, const uint64_t *
     }
 }
 
+// The same for u32 tile ids, four keys per thread from one 16-byte load; the
+// neighbours across threads come by shuffle, across warps by one extra load.
+__global__ void ranges4_kernel(const uint32_t *__restrict__ keys, uint64_t n_max, const uint64_t *n_dev,
+                               uint2 *ranges, uint32_t ntiles) {
+    const unsigned F = 0xffffffffu;
+    const uint32_t none = 0xffffffffu;  // no tile id
+    const uint64_t n = n_dev ? (*n_dev > n_max ? 0 : *n_dev) : n_max;
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); 4 * base < n; base += stride) {
+        const uint64_t i0 = 4 * (base + lane);  // the loop is warp-uniform
+        uint32_t k[4];
+        if (i0 + 4 <= n) {
+            const uint4 v = reinterpret_cast<const uint4 *>(keys)[i0 / 4];  // 256-byte aligned buffer
+            k[0] = v.x, k[1] = v.y, k[2] = v.z, k[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? keys[i0 + j] : none;
+        }
+        uint32_t prev = __shfl_up_sync(F, k[3], 1), next = __shfl_down_sync(F, k[0], 1);
+        if (lane == 0) prev = i0 > 0 ? keys[i0 - 1] : none;  // i0 <= 4 base < n
+        if (lane == 31) next = i0 + 4 < n ? keys[i0 + 4] : none;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t t = k[j];
+            if (t >= ntiles) continue;  // past the end (none), or never for keys written by the emit kernels
+            const uint32_t p = j == 0 ? prev : k[j - 1], q = j == 3 ? next : k[j + 1];
+            if (p != t) ranges[t].x = (uint32_t)(i0 + j);
+            if (q != t) ranges[t].y = (uint32_t)(i0 + j + 1);
+        }
+    }
+}
+
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges, int ntiles,
                           cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
     if (e != cudaSuccess || n_max == 0) return e;
-    uint64_t blocks = (n_max + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    note_launch("ranges_kernel", s), ranges_kernel<KeyT><<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges, (uint32_t)ntiles);
+    if constexpr (sizeof(KeyT) == 4) {
+        uint64_t blocks = (n_max / 4 + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        if (blocks == 0) blocks = 1;
+        note_launch("ranges4_kernel", s), ranges4_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges,
+                                                                                          (uint32_t)ntiles);
+    } else {
+        uint64_t blocks = (n_max + 255) / 256;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        note_launch("ranges_kernel", s), ranges_kernel<KeyT><<<(unsigned)blocks, 256, 0, s>>>(keys, n_max, n_dev, ranges, (uint32_t)ntiles);
+    }
     return cudaGetLastError();
 }
 
