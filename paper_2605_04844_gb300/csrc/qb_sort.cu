@@ -61,11 +61,43 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const KeyT *__restrict__
     for (int j = threadIdx.x; j < total; j += blockDim.x) sh[j] = 0u;
     __syncthreads();
     const uint64_t n = device_count(n_dev, n_max);
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const KeyT k = keys[idx];
-        for (int p = 0; p < g.passes; ++p)
-            atomicAdd(&sh[off[p] + (int)((k >> g.shift[p]) & ((KeyT(1) << g.bits[p]) - 1))], 1u);
+    // Each thread takes 8 consecutive keys and adds a run of equal digits
+    // once: keys in emission order repeat their high digits (the tiles of
+    // one Gaussian), which would otherwise be conflicting shared atomics.
+    constexpr int J = 8;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * J;
+    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * J; i0 < n; i0 += stride) {
+        KeyT k[J];
+        if (sizeof(KeyT) == 4 && i0 + J <= n && (reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
+            // two 16-byte loads (i0 is a multiple of 8; callers' buffers may be unaligned)
+            const uint4 a = reinterpret_cast<const uint4 *>(keys + i0)[0];
+            const uint4 b = reinterpret_cast<const uint4 *>(keys + i0)[1];
+            k[0] = (KeyT)a.x, k[1] = (KeyT)a.y, k[2] = (KeyT)a.z, k[3] = (KeyT)a.w;
+            k[4] = (KeyT)b.x, k[5] = (KeyT)b.y, k[6] = (KeyT)b.z, k[7] = (KeyT)b.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < J; ++j) k[j] = i0 + j < n ? keys[i0 + j] : KeyT(0);
+        }
+        const int m = (int)(n - i0 < (uint64_t)J ? n - i0 : (uint64_t)J);
+        for (int p = 0; p < g.passes; ++p) {
+            const KeyT msk = (KeyT(1) << g.bits[p]) - 1;
+            const int sh_p = g.shift[p];
+            int run_d = (int)((k[0] >> sh_p) & msk);
+            uint32_t run_c = 1;
+#pragma unroll
+            for (int j = 1; j < J; ++j) {
+                if (j >= m) break;
+                const int d = (int)((k[j] >> sh_p) & msk);
+                if (d == run_d) {
+                    ++run_c;
+                } else {
+                    atomicAdd(&sh[off[p] + run_d], run_c);
+                    run_d = d;
+                    run_c = 1;
+                }
+            }
+            atomicAdd(&sh[off[p] + run_d], run_c);
+        }
     }
     __syncthreads();
     for (int p = 0; p < g.passes; ++p)
@@ -197,7 +229,7 @@ static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
         }
         size_t smem = 0;
         for (int p = 0; p < g.passes; ++p) smem += (size_t)4 << g.bits[p];
-        uint64_t hblocks = std::min<uint64_t>((n_max + 255) / 256, 152 * 4);
+        uint64_t hblocks = std::min<uint64_t>((n_max + 8 * 256 - 1) / (8 * 256), 152 * 4);
         note_launch("sort_hist_kernel", s), sort_hist_kernel<KeyT><<<(unsigned)hblocks, 256, smem, s>>>(keys, n_max, n_dev, g, hist);
         note_launch("sort_hist_scan_kernel", s), sort_hist_scan_kernel<<<g.passes, 1024, 0, s>>>(hist, g);
     }
