@@ -394,7 +394,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         const int tile_bits = frame->key_bits - kDepthBits;
         const int passes = tile_bits > 0 ? (tile_bits + frame->sort_digit_bits - 1) / frame->sort_digit_bits : 0;
         const uint32_t zero_off[1] = {0u};
-        QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), nullptr, frame_tileset(frame),
+        QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), frame_tileset(frame),
                                  zero_off, zero_off,
                                  at<uint2>(frame, L.ranges), sort_hist_table(at<void>(frame, L.sort_scratch)),
                                  sort_hist_stride(), frame->sort_digit_bits, tile_bits, frame->pair_capacity, s));

@@ -1174,14 +1174,13 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
 // gives each tile's count; an exclusive scan over the global tile ids gives
 // the ranges of the tile-sorted pairs; the counts summed per digit give the
 // exclusive bucket offsets of every pass of the tile sort.  One block.
-__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, const uint32_t *counts,
-                                                         TileSet ts, TileOffsets off, uint2 *ranges, uint32_t *hist,
+__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, TileSet ts, TileOffsets off, uint2 *ranges, uint32_t *hist,
                                                          int hist_stride, int rb, PassGeo g, uint64_t capacity) {
     extern __shared__ uint32_t sh_hist[];  // passes x 2^rb
     const int R = 1 << rb, passes = g.passes;
     for (int j = threadIdx.x; j < passes * R; j += blockDim.x) sh_hist[j] = 0u;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int c = 0; c < (counts ? 0 : ts.n_cams); ++c) {
+    for (int c = 0; c < ts.n_cams; ++c) {
         const int tx = ts.cam[c].tiles_x, ty = ts.cam[c].tiles_y, stride = tx + 1;
         int *Dc = D + off.diff[c];
         const int *Sc = single + off.single[c];
@@ -1222,7 +1221,6 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
     const int per = (ntiles + blockDim.x - 1) / blockDim.x;
     const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
     auto count_of = [&](int t) -> uint32_t {
-        if (counts) return counts[t];
         const int c = camera_of(ts, (uint32_t)t);
         const int lt = t - (int)ts.cam[c].tile_base, tx = ts.cam[c].tiles_x;
         return (uint32_t)D[off.diff[c] + (lt / tx) * (tx + 1) + lt % tx];
@@ -1260,7 +1258,7 @@ __global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *sing
     }
 }
 
-cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint32_t *counts, const TileSet &ts,
+cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileSet &ts,
                              const uint32_t *diff_off, const uint32_t *single_off, uint2 *ranges, uint32_t *hist,
                              int hist_stride, int digit_bits, int tile_bits, uint64_t capacity, cudaStream_t s) {
     const PassGeo g = pass_geo(tile_bits, digit_bits);
@@ -1271,7 +1269,7 @@ cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint3
         off.single[c] = c < ts.n_cams ? single_off[c] : 0u;
     }
     const size_t smem = (size_t)passes * ((size_t)1 << digit_bits) * 4;
-    note_launch("tile_prep_kernel", s), tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, counts, ts, off, ranges, hist,
+    note_launch("tile_prep_kernel", s), tile_prep_kernel<<<1, 1024, smem, s>>>(tile_diff, tile_single, ts, off, ranges, hist,
                                                           hist_stride, digit_bits, g, capacity);
     return cudaGetLastError();
 }

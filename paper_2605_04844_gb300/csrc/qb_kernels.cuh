@@ -179,9 +179,9 @@ cudaError_t launch_expand_ranges(const uint2 *ranges, int ntiles, uint32_t *out,
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges, int ntiles,
                           cudaStream_t s);
-// Ranges and every tile-sort pass's bucket offsets from per-tile counts: the
-// preprocess's difference arrays (counts null) or a count array.
-cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const uint32_t *counts, const TileSet &ts,
+// Ranges and every tile-sort pass's bucket offsets from the per-tile counts
+// in the preprocess's difference arrays (the fused-emit frame path).
+cudaError_t launch_tile_prep(int *tile_diff, const int *tile_single, const TileSet &ts,
                              const uint32_t *diff_off, const uint32_t *single_off, uint2 *ranges, uint32_t *hist,
                              int hist_stride, int digit_bits, int tile_bits, uint64_t capacity, cudaStream_t s);
 // Per-tile counts of n tile ids into counts[0, ntiles) (counts and the
