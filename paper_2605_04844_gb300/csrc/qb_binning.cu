@@ -1174,7 +1174,8 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
 // gives each tile's count; an exclusive scan over the global tile ids gives
 // the ranges of the tile-sorted pairs; the counts summed per digit give the
 // exclusive bucket offsets of every pass of the tile sort.  One block.
-__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, TileSet ts, TileOffsets off, uint2 *ranges, uint32_t *hist,
+__global__ void __launch_bounds__(1024) tile_prep_kernel(int *D, const int *single, TileSet ts, TileOffsets off,
+                                                         uint2 *ranges, uint32_t *hist,
                                                          int hist_stride, int rb, PassGeo g, uint64_t capacity) {
     extern __shared__ uint32_t sh_hist[];  // passes x 2^rb
     const int R = 1 << rb, passes = g.passes;
