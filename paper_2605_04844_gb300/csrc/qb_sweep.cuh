@@ -195,7 +195,8 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
     for (int j = 0; j < PER; ++j) {
         int d = tid * PER + j;
         if (d >= R) continue;
-        s_lstart[d] = run;
+        const uint32_t lstart = run;
+        s_lstart[d] = lstart;
         run += cnt[j];
         uint32_t acc = 0;
         if (tile > 0) {
@@ -234,7 +235,9 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
             }
             st_relaxed(lb + d, kFlagIncl | ((acc + cnt[j]) & kCountMask));
         }
-        s_gbase[d] = bin_off[d] + acc;
+        // output position of the tile's j-th key in block order: s_gbase[d] + j
+        // (the digit's global base minus its start in the block; mod 2^32)
+        s_gbase[d] = bin_off[d] + acc - lstart;
     }
     __syncthreads();
 
@@ -268,7 +271,7 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
             if (j < tcount) {
                 const uint2 kv = s_pairs[j];
                 const uint32_t d = (kv.x >> shift) & mask;
-                const uint32_t dest = s_gbase[d] + (j - s_lstart[d]);
+                const uint32_t dest = s_gbase[d] + j;
                 if (dest < n) {  // dest >= n only after a look-back timeout
                     if (WRITE_KEYS) kout[dest] = (KeyT)kv.x;
                     vout[dest] = kv.y;
@@ -296,7 +299,7 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
             if (j < tcount) {
                 const KeyT kk = s_keys[j];
                 const uint32_t d = (uint32_t)(kk >> shift) & mask;
-                dest[k] = s_gbase[d] + (j - s_lstart[d]);
+                dest[k] = s_gbase[d] + j;
                 if (WRITE_KEYS && dest[k] < n) kout[dest[k]] = kk;
             }
         }
