@@ -3,6 +3,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "qb_kernels.cuh"
@@ -188,6 +190,20 @@ void note_launch(const char *kernel, cudaStream_t s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     const qb_launch_hook h = g_hook.load(std::memory_order_acquire);
     if (h) h(kernel, (qb_stream_t)s, g_hook_user.load(std::memory_order_relaxed));
+}
+
+cudaError_t ensure_dyn_smem(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = set[{func, dev}];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 }  // namespace qb
 

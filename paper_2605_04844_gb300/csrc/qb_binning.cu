@@ -441,14 +441,9 @@ __global__ void __launch_bounds__(kSortBlock) emit_sweep_kernel(EmitArgs a, uint
 template <int RB, bool WRITE_KEYS>
 static cudaError_t launch_emit_sweep_b(const EmitArgs &a, uint32_t *kout, uint32_t *vout, const uint32_t *bin_off,
                                        uint32_t *lookback, uint32_t *counter, uint32_t mask, cudaStream_t s) {
-    static bool attrs = false;
     constexpr size_t smem = emit_sweep_smem<RB>();
-    if (!attrs) {
-        cudaError_t e = cudaFuncSetAttribute(emit_sweep_kernel<RB, WRITE_KEYS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attrs = true;
-    }
+    cudaError_t e = ensure_dyn_smem((const void *)emit_sweep_kernel<RB, WRITE_KEYS>, smem);
+    if (e != cudaSuccess) return e;
     const uint64_t pairs = a.n_pairs_host != UINT64_MAX ? a.n_pairs_host : a.capacity;
     uint64_t blocks = (pairs + kSortTile - 1) / kSortTile;
     if (blocks == 0) blocks = 1;  // one block still flags an overflow
@@ -959,20 +954,9 @@ cudaError_t launch_chunked(const EmitArgs &e, const ChunkArgs &a, uint2 *ranges,
                                                                                 a.chunk_pairs, e.n_pairs, a.start);
     const size_t smem_count = (size_t)kBandWarps * a.band_diff_ints * 4;
     const size_t smem_emit = (size_t)kBandWarps * ((size_t)a.band_words * 4 + sizeof(SegTable));
-    static size_t set_count = 0, set_emit = 0;
     cudaError_t err;
-    if (smem_count > set_count) {
-        if ((err = cudaFuncSetAttribute(chunk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem_count)) != cudaSuccess)
-            return err;
-        set_count = smem_count;
-    }
-    if (smem_emit > set_emit) {
-        if ((err = cudaFuncSetAttribute(chunk_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem_emit)) != cudaSuccess)
-            return err;
-        set_emit = smem_emit;
-    }
+    if ((err = ensure_dyn_smem((const void *)chunk_count_kernel, smem_count)) != cudaSuccess) return err;
+    if ((err = ensure_dyn_smem((const void *)chunk_emit_kernel, smem_emit)) != cudaSuccess) return err;
     note_launch("chunk_gather_kernel", s), chunk_gather_kernel<<<(e.n + 255) / 256, 256, 0, s>>>(a, e.n);
     const dim3 bg((a.n_bands + kBandWarps - 1) / kBandWarps, a.n_chunks);
     note_launch("chunk_count_kernel", s), chunk_count_kernel<<<bg, kBandWarps * 32, smem_count, s>>>(a);
@@ -1150,13 +1134,7 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
     if (e != cudaSuccess || ntiles == 0) return e;
     // the histogram; for the last block's prep also the total and the digit sums
     const size_t smem = 4 * ((size_t)ntiles + 1 + ((size_t)1 << kMaxDigitBits));
-    static size_t set = 0;
-    if (smem > set) {
-        if ((e = cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-            return e;
-        set = smem;
-    }
+    if ((e = ensure_dyn_smem((const void *)tile_count_kernel, smem)) != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -59,6 +59,10 @@ void set_last_error(const char *msg);
 // Counts one kernel launch of the library (qb_kernel_launches) and reports
 // it to the launch hook, if one is set, just before the launch on stream s.
 void note_launch(const char *kernel, cudaStream_t s);
+// Raises kernel func's dynamic shared-memory limit on the current device to
+// at least bytes; the limit set is remembered per (kernel, device), and the
+// calls are safe from several host threads.
+cudaError_t ensure_dyn_smem(const void *func, size_t bytes);
 
 // ---- sort -------------------------------------------------------------------
 // Digit geometry of an LSD radix sort on bits [0, end_bit) with digits of at

@@ -165,14 +165,9 @@ static cudaError_t launch_pass_t(const KeyT *kin, const uint32_t *vin, KeyT *kou
                                  const uint64_t *n_dev, const uint32_t *bin_off, uint32_t *lookback,
                                  uint32_t *counter, int shift, uint32_t mask, uint32_t *err, const char *name,
                                  cudaStream_t s) {
-    static bool attrs = false;
     constexpr size_t smem = sweep_smem<RB, KeyT>();
-    if (!attrs) {
-        cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<RB, KeyT, WRITE_KEYS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attrs = true;
-    }
+    cudaError_t e = ensure_dyn_smem((const void *)onesweep_kernel<RB, KeyT, WRITE_KEYS>, smem);
+    if (e != cudaSuccess) return e;
     note_launch(name, s), onesweep_kernel<RB, KeyT, WRITE_KEYS><<<(unsigned)sort_tiles(n_max), kSortBlock, smem, s>>>(
         kin, vin, kout, vout, n_max, n_dev, bin_off, lookback, counter, shift, mask, err);
     return cudaGetLastError();
@@ -220,13 +215,8 @@ static cudaError_t sort_impl(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
     if (e != cudaSuccess || n_max == 0) return e;
 
     if (!hist_ready) {
-        static bool attrs = false;
-        if (!attrs) {
-            e = cudaFuncSetAttribute(sort_hist_kernel<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kMaxPasses * kHistStride * 4);
-            if (e != cudaSuccess) return e;
-            attrs = true;
-        }
+        e = ensure_dyn_smem((const void *)sort_hist_kernel<KeyT>, (size_t)kMaxPasses * kHistStride * 4);
+        if (e != cudaSuccess) return e;
         size_t smem = 0;
         for (int p = 0; p < g.passes; ++p) smem += (size_t)4 << g.bits[p];
         uint64_t hblocks = std::min<uint64_t>((n_max + 8 * 256 - 1) / (8 * 256), 152 * 4);
