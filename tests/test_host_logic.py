@@ -74,7 +74,9 @@ def test_kernel_work_figures():
 
 
 def test_roofline_picks_the_dominant_kernel_and_uses_the_measured_peaks():
-    peaks = json.load(open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")))
+    path = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    # the driver writes the measured peaks; without them bench.py falls back to 6800 GB/s
+    peaks = json.load(open(path)) if os.path.exists(path) else {"hbm_gbs": 6800.0}
     P, n, E = 20_000_000, 600_000, 400_000_000
     kernels = {
         "render_kernel": {"ms_per_launch": 0.30, "ms_per_step": 0.30},
