@@ -405,8 +405,8 @@ def kernel_work(P, n, n_eval):
 # captured (kernel -> (unit, bytes per unit)).
 TRAFFIC_PER_UNIT = {
     "render_kernel": ("eval", (12.206848e6 + 1.605376e6) / 398728138),
-    "tile_sort_pass": ("pair", (166.167808e6 + 118.349568e6) / 20633099),
-    "tile_sort_pass_values": ("pair", (165.426688e6 + 30.919168e6) / 20633099),
+    "tile_sort_pass": ("pair", (166.163712e6 + 120.412416e6) / 20633099),
+    "tile_sort_pass_values": ("pair", (165.441280e6 + 31.980032e6) / 20633099),
     "emit_warp_kernel": ("pair", (51.835392e6 + 120.607488e6) / 20633099),
     "tile_count_kernel": ("pair", (82.601216e6 + 1.472768e6) / 20633099),
 }
