@@ -73,8 +73,8 @@ typedef enum {
  * identical sorted values and ranges.
  *  DEPTH_FIRST  (default) sort the n Gaussians by (depth, index) once, emit
  *               each Gaussian's pairs in that order with 32-bit tile keys, then
- *               stable-sort the pairs on the tile bits only (the emit runs the
- *               first digit pass itself).
+ *               stable-sort the pairs on the tile bits only (with emit_fused
+ *               the emit runs the first digit pass itself).
  *  FULL_KEY     emit in index order with 64-bit keys (tile << 31) | depth
  *               bits and stable-sort on all 31 + tile bits (SortPairs, Sec. 2).
  *  CHUNKED      depth order as DEPTH_FIRST, then a counting placement instead
@@ -243,10 +243,11 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
  * key = (tile << 31) | float bits of the depth (FULL_KEY) or the tile id
  * (DEPTH_FIRST, after sorting the Gaussians by depth), value = Gaussian
  * index, in emission order (each Gaussian's pairs at its scan offset).  In
- * DEPTH_FIRST the per-tile counts give the ranges here, and in the QPass
- * modes the emit also performs the first digit pass of the tile sort, so the
- * pairs leave it bucketed by their lowest tile digit rather than in emission
- * order.
+ * DEPTH_FIRST with emit_fused the per-tile counts (from the preprocess) give
+ * the ranges here, and in the QPass modes the emit also performs the first
+ * digit pass of the tile sort, so the pairs leave it bucketed by their lowest
+ * tile digit rather than in emission order; without emit_fused (the default)
+ * qb_sort counts the emitted tile ids.
  * If n_pairs_out is non-NULL the host synchronises once to read P, stores it
  * in *n_pairs_out and frame->n_pairs, and returns CAPACITY (writing no pairs)
  * when P > pair_capacity.  With NULL nothing synchronises; an overflow is
@@ -255,9 +256,11 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
 
 /* Stage 3 (Sec. 2 "SortPairs"): stable LSD radix sort of the pairs with the
  * library's onesweep sort on the key bits [0, 31 + tile bits) (FULL_KEY),
- * then the per-tile [start, end) ranges; or the remaining digit passes on
- * the tile bits (DEPTH_FIRST), whose last pass writes only the values (in
- * vals, sorted_in_alt = 0). */
+ * then the per-tile [start, end) ranges; or (DEPTH_FIRST) a histogram of
+ * the emitted tile ids giving the ranges and every pass's bucket offsets
+ * (unless the fused emit already did), then the remaining digit passes on
+ * the tile bits, whose last pass writes only the values (in vals,
+ * sorted_in_alt = 0). */
 qb_status qb_sort(qb_frame *frame, qb_stream_t stream);
 
 /* Stage 4 (Sec. 2 "Render", Eq. 2): front-to-back compositing per pixel.
@@ -360,8 +363,9 @@ qb_status qb_batch_init(qb_batch *batch, int32_t n, int32_t n_cams, const int32_
 
 /* Forward of every camera of the batch:
  * per group, one preprocess over all (camera, Gaussian) records, depth
- * order, scan, per-tile counts, QPass emit with global tile ids, tile sort
- * and one persistent render over the group's tiles.  cams: host array of
+ * order, scan, QPass emit with tile ids global over the group, a stable sort
+ * on those ids, the ranges from the sorted ids, and one persistent render
+ * over the group's tiles.  cams: host array of
  * n_cams cameras whose sizes match qb_batch_init; tune: host, NULL for
  * defaults; d_images: device floats, total_floats of them.  No host
  * synchronisation and no allocation, so a call can be captured in a CUDA
