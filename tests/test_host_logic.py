@@ -98,3 +98,14 @@ def test_roofline_picks_the_dominant_kernel_and_uses_the_measured_peaks():
     assert sp["achieved"] == pytest.approx(16 * P / 0.10e-3 / 1e9, rel=1e-3)
     assert sp["traffic"] == int(bench.TRAFFIC_PER_UNIT["tile_sort_pass"][1] * P)
     assert "not_a_kernel_of_ours" not in r["kernels"]
+
+
+def test_autotune_cache_round_trip_and_corrupt_file(tmp_path, monkeypatch):
+    from paper_2605_04844_gb300 import autotune
+    monkeypatch.setenv("QUADBOX_CACHE_DIR", str(tmp_path / "cache"))
+    assert autotune._load() == {}  # no file yet
+    db = {"GB300|n=10|64x48|quadbox": {"digit_bits": 9, "ms": {"8": 1.0, "9": 0.9}}}
+    autotune._save(db)
+    assert autotune._load() == db
+    (tmp_path / "cache" / "tune.json").write_text("{ not json")
+    assert autotune._load() == {}  # a damaged cache is ignored, not fatal
