@@ -350,10 +350,10 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded 1M-Gaussian clustered scene; stands in for Mip-NeRF 360 / DB / T&T)",
-        "config": {"workload": "1M Gaussians, 1920x1080, SH degree 3, 16x16 tiles, QuadBox binning (clamped to "
-                               "3-sigma) vs 3-sigma AABB on the same kernels",
+        "config": {"workload": "1M Gaussians, 1920x1080, SH3, 16x16 tiles (C2): QuadBox vs 3-sigma AABB binning, "
+                               "same kernels",
                    "n_gaussians": n, "width": W, "height": H, "sh_degree": 3,
-                   "l2": "L2 flushed (258 MB write) between timed steps; scene inputs 236 MB > L2",
+                   "l2": "flushed between timed steps (258 MB write); scene 236 MB > L2",
                    "sort_digit_bits": digit_bits, "sort_mode": args.sort_mode,
                    "parallelism": f"replicas x{world}"},
         "quadbox": {"fwd_fps": round(1000.0 / fwd_ms, 2), "fwd_ms": round(fwd_ms, 4),
@@ -372,7 +372,10 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed": round(wall, 2),
     }
-    result["roofline"] = roofline(fwd_stages, fwd_kernels, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    result["roofline"] = roofline(fwd_stages, fwd_kernels, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode,
+                                  sms=sms)
+    result["roofline_kernels"] = result["roofline"].pop("kernels", {})
     result["kernels_fwd"] = fwd_kernels
     # counted by the library at each launch, inside the timed steps of every
     # phase and of the end-to-end loop
@@ -412,7 +415,7 @@ TRAFFIC_PER_UNIT = {
 }
 
 
-def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode):
+def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode, sms=152):
     """Roofline of the dominant kernel of the forward step: its algorithmic
     work per launch over its average launch duration, both measured in the
     timed steps (CUDA events recorded at each launch on the launching
@@ -424,7 +427,7 @@ def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
     work = kernel_work(P, n, n_eval)
     rows = {}
     for name, k in kernels.items():
@@ -455,7 +458,7 @@ def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode
     out = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
            "frac": d["frac"], "traffic": traffic,
            "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if d["bound"] == "hbm" else
-                           f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median sampled SM clock)"),
+                           f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median sampled SM clock)"),
            "kernels": rows}
     return out
 
@@ -809,8 +812,8 @@ def cpu_baseline(scene_np, cam):
     O.set_threads(cores)
     c1_all = oracle_frame_seconds(c1_scene, c1_cam, row_stride=1)[0]
     return {"value": round(1.0 / secs, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one 1M-Gaussian 1920x1080 QuadBox frame: FP64 projection, binning and sort in full, "
-                      f"compositing of every 16th tile row ({npx} pixels) scaled to the frame",
+            "sample": f"the C2 frame in FP64: projection, binning, sort in full; every 16th tile row "
+                      f"composited ({npx} px), scaled",
             "seconds_per_frame": round(secs, 3),
             "one_core_seconds_per_frame": round(secs1, 3),
             "one_core_sample": f"the same frame with every 64th tile row composited ({npx1} pixels), scaled",
@@ -845,6 +848,67 @@ def run_reference(args):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# Sections of the full result printed on their own lines before the headline
+# (and kept whole in the --out file).
+DETAIL_SECTIONS = ("kernels_fwd", "roofline_kernels", "quadbox_other_sort_modes", "autotune", "c4_fwd_bwd",
+                   "binning_modes", "c3_zoom", "batch64", "cpu_baseline_detail")
+
+HEADLINE_MAX_BYTES = 2000
+
+
+def output_lines(res):
+    """The lines the run prints: each detail section on its own line, then
+    the compact headline last (the line a reader of the output tail parses)."""
+    lines = [json.dumps({"section": name, name: res[name]}) for name in DETAIL_SECTIONS if name in res]
+    lines.append(json.dumps(headline(res)))
+    return lines
+
+
+def headline(res):
+    """The compact last line of the run: the headline metric, the QuadBox and
+    3-sigma AABB forward and forward+backward times with their pairs per
+    frame, the end-to-end rate, clocks, the dominant kernel's roofline row
+    and the CPU oracle baseline; everything else is in the detail lines."""
+    h = {k: res[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                             "higher_is_better", "scaling", "vs_baseline", "dtype", "data") if k in res}
+    cfg = res.get("config", {})
+    h["config"] = {k: cfg[k] for k in ("workload", "n_gaussians", "width", "height", "sh_degree", "l2",
+                                       "sort_digit_bits", "parallelism") if k in cfg}
+    for side in ("quadbox", "aabb3s"):
+        if side in res:
+            h[side] = {k: res[side][k] for k in ("fwd_ms", "fwd_bwd_ms", "pairs_per_frame") if k in res[side]}
+    if "stage_ms" in res.get("quadbox", {}):
+        h["quadbox"]["stage_ms"] = res["quadbox"]["stage_ms"]
+    for k in ("speedup_vs_aabb", "e2e", "gpu_launches"):
+        if k in res:
+            h[k] = res[k]
+    clk = res.get("clocks") or {}
+    h["clocks"] = {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    rf = res.get("roofline") or {}
+    h["roofline"] = {k: rf.get(k) for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")}
+    if "peak_source" in rf:
+        h["roofline"]["peak_source"] = rf["peak_source"]
+    cb = res.get("cpu_baseline")
+    if cb:
+        h["cpu_baseline"] = {k: cb.get(k) for k in ("value", "unit", "cores", "kind", "sample")}
+    b = res.get("batch64")
+    if b:
+        h["batch64"] = {k: b.get(k) for k in ("graph_fwd_ms", "graph_fwd_bwd_ms", "speedup_fwd", "speedup_fwd_bwd")}
+    h["paper_context"] = "paper: 1.85x FPS over 3DGS on NVIDIA A100 (Table 1)"
+    h["details"] = "sections on the preceding output lines"
+    # optional keys go first when the line would grow past the bound
+    for k in ("paper_context", "details", "batch64", ("roofline", "peak_source"), ("quadbox", "stage_ms")):
+        if len(json.dumps(h)) <= HEADLINE_MAX_BYTES:
+            break
+        if isinstance(k, tuple):
+            h.get(k[0], {}).pop(k[1], None)
+        else:
+            h.pop(k, None)
+    if "cpu_baseline" in h and len(json.dumps(h)) > HEADLINE_MAX_BYTES:
+        h["cpu_baseline"]["sample"] = h["cpu_baseline"]["sample"][:120]
+    return h
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -875,11 +939,11 @@ def main():
             from paper_2605_04844_gb300 import synth
             scene_np, cam = synth.config2(args.n, args.width, args.height)
             res["cpu_baseline"] = cpu_baseline(scene_np, cam)
-        line = json.dumps(res)
-        print(line, flush=True)
         if args.out:
             with open(args.out, "w") as f:
-                f.write(line + "\n")
+                f.write(json.dumps(res) + "\n")
+        for line in output_lines(res):
+            print(line, flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
