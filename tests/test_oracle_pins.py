@@ -354,6 +354,87 @@ def test_conservative_bruteforce():
             assert tiles <= set(Q[i]), f"Gaussian {i}: uncovered tiles {sorted(tiles - set(Q[i]))[:5]}"
 
 
+def _three_sigma_scene():
+    """The adversarial scene plus isotropic Gaussians of several sizes (equal
+    eigenvalues: the discriminant floor of the radius binds there)."""
+    sc, cam = adversarial_scene(n=1200, seed=44)
+    iso = 40
+    rng = np.random.default_rng(45)
+    z = rng.uniform(1.5, 6.0, iso)
+    xy = rng.uniform(-0.3, 0.3, (iso, 2)) * z[:, None]
+    means = np.concatenate([xy, z[:, None]], axis=1)
+    s = np.repeat(rng.uniform(-4.0, -1.0, iso)[:, None], 3, axis=1)  # equal log-scales
+    quats = np.tile([1.0, 0.0, 0.0, 0.0], (iso, 1))
+    sc = dict(sc)
+    for k, v in (("means", means), ("scales", s), ("quats", quats), ("opacities", np.full(iso, 2.0)),
+                 ("sh", np.zeros((iso,) + sc["sh"].shape[1:]))):
+        sc[k] = np.concatenate([np.asarray(sc[k], np.float64), v.astype(np.float64)])
+    return sc, cam, iso
+
+
+def test_3sigma_radius_against_eigenvalues():
+    """The vanilla box of Sec. 2 has side 6 sqrt(lambda_max), lambda_max the
+    largest eigenvalue of Sigma^2D: the oracle's integer radius is
+    ceil(3 sqrt(lambda_max)) with lambda_max from numpy's symmetric eigen-
+    solver.  The discriminant of the 2x2 eigenvalue formula is floored at 0.1
+    (the 3DGS convention, reading C2): where ((l1 - l2) / 2)^2 < 0.1 the
+    radius is ceil(3 sqrt(trace / 2 + sqrt(0.1))), which still covers
+    lambda_max."""
+    sc, cam, iso = _three_sigma_scene()
+    proj = O.project(sc, cam)
+    checked = floored = 0
+    for i, p in enumerate(proj):
+        if p[O.F_VALID] == 0:
+            continue
+        S = np.array([[p[O.F_S11], p[O.F_S12]], [p[O.F_S12], p[O.F_S22]]])
+        lam = np.linalg.eigvalsh(S)  # ascending
+        half_gap2 = (0.5 * (lam[1] - lam[0])) ** 2
+        if half_gap2 >= 0.1 * (1 + 1e-9):
+            want = 3.0 * math.sqrt(lam[1])
+        elif half_gap2 <= 0.1 * (1 - 1e-9):
+            want = 3.0 * math.sqrt(0.5 * (lam[0] + lam[1]) + math.sqrt(0.1))
+            assert want >= 3.0 * math.sqrt(lam[1])
+            floored += 1
+        else:
+            continue
+        if abs(want - round(want)) < 1e-9:
+            continue  # ceil undecidable at the rounding of the eigenvalues
+        assert p[O.F_R3] == math.ceil(want), f"Gaussian {i}: r3 {p[O.F_R3]} vs ceil({want})"
+        checked += 1
+    assert checked > 1000 and floored >= iso
+
+
+def test_3sigma_rect_holds_the_3sigma_ellipse_bruteforce():
+    """Every pixel centre inside the 3-sigma ellipse d^T Sigma^-1 d <= 9 (the
+    inverse by numpy, not the oracle's conic) lies in the 3-sigma pixel
+    interval [ceil(mu) - r3, floor(mu) + r3] on both axes and in a tile of the
+    AABB3S tile set, and the interval is no wider than one pixel plus
+    3 sqrt(lambda_max) on each side (so r3 is not inflated either)."""
+    sc, cam, _ = _three_sigma_scene()
+    W, H = cam["width"], cam["height"]
+    tx, _ = O.grid(W, H)
+    proj = O.project(sc, cam)
+    S3 = tile_sets(O.rects_f64(proj, O.AABB3S, True, W, H), True, tx)
+    ys, xs = np.mgrid[0:H, 0:W]
+    inside_px = 0
+    for i, p in enumerate(proj):
+        if p[O.F_VALID] == 0:
+            continue
+        S = np.array([[p[O.F_S11], p[O.F_S12]], [p[O.F_S12], p[O.F_S22]]])
+        Si = np.linalg.inv(S)
+        dx, dy = xs - p[O.F_X], ys - p[O.F_Y]
+        m = Si[0, 0] * dx * dx + 2 * Si[0, 1] * dx * dy + Si[1, 1] * dy * dy
+        hit = m <= 9.0
+        r3 = p[O.F_R3]
+        assert np.all(np.abs(dx[hit]) <= r3) and np.all(np.abs(dy[hit]) <= r3), f"Gaussian {i}"
+        tiles = set(((ys[hit] // 16) * tx + xs[hit] // 16).tolist())
+        assert tiles <= set(S3[i]), f"Gaussian {i}: 3-sigma pixels outside the AABB3S tiles"
+        inside_px += int(hit.sum())
+        lmax = np.linalg.eigvalsh(S)[1]
+        assert r3 <= 3.0 * math.sqrt(lmax + math.sqrt(0.1)) + 1.0
+    assert inside_px > 10000
+
+
 def test_dualbox_is_not_conservative():
     sc, cam = adversarial_scene(n=1200, seed=33)
     W, H = cam["width"], cam["height"]
