@@ -646,75 +646,134 @@ void orc_render_brute(int W, int H, int n, const int32_t *rects, const double *p
 /* (zero derivative where the 0.99 cap is active).  dL/dconic is w.r.t. the */
 /* three numbers (a, b, c) as they appear in q.                              */
 /* ------------------------------------------------------------------------ */
+/* One pixel's share of the backward: the forward walk over its tile list
+ * (recording every counted entry), then, per counted entry k, the colour
+ * behind it S_k = sum_{i>k} T_i alpha_i c_i + T_final bg and the gradient
+ * of sum_ch g_ch C_ch through alpha_k (Eq. 2 differentiated), chained to o,
+ * the conic and mu^2D.  acc_* are caller-provided buffers of the tile list's
+ * length. */
+typedef struct {
+    int32_t *id;
+    double *T, *a, *G, *dx, *dy;
+    int *cap;
+} orc_bwd_scratch;
+
+static void backward_pixel(int px, int py, const int32_t *ids, int64_t cnt, const double *proj,
+                           const double *bg, const double g[3], orc_bwd_scratch *w, double *g_xy,
+                           double *g_conic, double *g_o, double *g_rgb)
+{
+    double T = 1.0;
+    int m = 0;
+    for (int64_t k = 0; k < cnt; ++k) {
+        const double *p = proj + (size_t)ORC_NF * ids[k];
+        double dx = p[F_X] - px, dy = p[F_Y] - py;
+        double q = p[F_A] * dx * dx + 2.0 * p[F_B] * dx * dy + p[F_C] * dy * dy;
+        double power = -0.5 * q;
+        if (power > 0.0) continue;
+        double G = exp(power);
+        double alpha = fmin(0.99, p[F_O] * G);
+        if (alpha < ALPHA_MIN) continue;
+        double testT = T * (1.0 - alpha);
+        if (testT < 1e-4) break;
+        w->id[m] = ids[k]; w->T[m] = T; w->a[m] = alpha; w->G[m] = G;
+        w->dx[m] = dx; w->dy[m] = dy; w->cap[m] = (p[F_O] * G >= 0.99);
+        ++m;
+        T = testT;
+    }
+    for (int k = 0; k < m; ++k) {
+        const double *p = proj + (size_t)ORC_NF * w->id[k];
+        double behind[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            double sacc = T * bg[ch];
+            for (int i = k + 1; i < m; ++i) {
+                const double *pi = proj + (size_t)ORC_NF * w->id[i];
+                sacc += w->T[i] * w->a[i] * pi[F_R + ch];
+            }
+            behind[ch] = sacc;
+        }
+        double dL_dalpha = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            g_rgb[3 * (size_t)w->id[k] + ch] += w->T[k] * w->a[k] * g[ch];
+            dL_dalpha += g[ch] * (w->T[k] * p[F_R + ch] - behind[ch] / (1.0 - w->a[k]));
+        }
+        if (w->cap[k]) continue;
+        double G = w->G[k], o = p[F_O];
+        g_o[w->id[k]] += G * dL_dalpha;
+        double dL_dq = dL_dalpha * o * G * (-0.5);
+        double dx = w->dx[k], dy = w->dy[k];
+        g_conic[3 * (size_t)w->id[k] + 0] += dL_dq * dx * dx;
+        g_conic[3 * (size_t)w->id[k] + 1] += dL_dq * 2.0 * dx * dy;
+        g_conic[3 * (size_t)w->id[k] + 2] += dL_dq * dy * dy;
+        g_xy[2 * (size_t)w->id[k] + 0] += dL_dq * 2.0 * (p[F_A] * dx + p[F_B] * dy);
+        g_xy[2 * (size_t)w->id[k] + 1] += dL_dq * 2.0 * (p[F_B] * dx + p[F_C] * dy);
+    }
+}
+
+static int bwd_scratch_alloc(orc_bwd_scratch *w, int64_t maxlen)
+{
+    size_t n = (size_t)(maxlen + 1);
+    w->id = (int32_t *)malloc(sizeof(int32_t) * n);
+    w->T = (double *)malloc(sizeof(double) * n);
+    w->a = (double *)malloc(sizeof(double) * n);
+    w->G = (double *)malloc(sizeof(double) * n);
+    w->dx = (double *)malloc(sizeof(double) * n);
+    w->dy = (double *)malloc(sizeof(double) * n);
+    w->cap = (int *)malloc(sizeof(int) * n);
+    return w->id && w->T && w->a && w->G && w->dx && w->dy && w->cap;
+}
+
+static void bwd_scratch_free(orc_bwd_scratch *w)
+{
+    free(w->id); free(w->T); free(w->a); free(w->G); free(w->dx); free(w->dy); free(w->cap);
+}
+
+static int64_t longest_list(int W, int H, const int64_t *ranges)
+{
+    int ntiles = ((W + ORC_TILE - 1) / ORC_TILE) * ((H + ORC_TILE - 1) / ORC_TILE);
+    int64_t maxlen = 0;
+    for (int t = 0; t < ntiles; ++t)
+        if (ranges[2 * t + 1] - ranges[2 * t] > maxlen) maxlen = ranges[2 * t + 1] - ranges[2 * t];
+    return maxlen;
+}
+
+/* Gradients of sum(dL_dimg * image) w.r.t. mu^2D, the conic, o and the
+ * colour, accumulated over every pixel (dL_dimg planar [3][H][W]). */
 void orc_render_backward(int W, int H, const int64_t *ranges, const int32_t *vals, const double *proj,
                          const double *bg, const double *dL_dimg, double *g_xy, double *g_conic,
                          double *g_o, double *g_rgb)
 {
     int tiles_x = (W + ORC_TILE - 1) / ORC_TILE;
-    int64_t maxlen = 0;
-    int ntiles = tiles_x * ((H + ORC_TILE - 1) / ORC_TILE);
-    for (int t = 0; t < ntiles; ++t)
-        if (ranges[2 * t + 1] - ranges[2 * t] > maxlen) maxlen = ranges[2 * t + 1] - ranges[2 * t];
-    int32_t *acc_id = (int32_t *)malloc(sizeof(int32_t) * (size_t)(maxlen + 1));
-    double *acc_T = (double *)malloc(sizeof(double) * (size_t)(maxlen + 1));
-    double *acc_a = (double *)malloc(sizeof(double) * (size_t)(maxlen + 1));
-    double *acc_G = (double *)malloc(sizeof(double) * (size_t)(maxlen + 1));
-    double *acc_dx = (double *)malloc(sizeof(double) * (size_t)(maxlen + 1));
-    double *acc_dy = (double *)malloc(sizeof(double) * (size_t)(maxlen + 1));
-    int *acc_cap = (int *)malloc(sizeof(int) * (size_t)(maxlen + 1));
+    orc_bwd_scratch w;
+    if (!bwd_scratch_alloc(&w, longest_list(W, H, ranges))) { bwd_scratch_free(&w); return; }
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px) {
             int t = (py / ORC_TILE) * tiles_x + px / ORC_TILE;
-            int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
-            double T = 1.0;
-            int m = 0;
-            for (int64_t k = s; k < e; ++k) {
-                const double *p = proj + (size_t)ORC_NF * vals[k];
-                double dx = p[F_X] - px, dy = p[F_Y] - py;
-                double q = p[F_A] * dx * dx + 2.0 * p[F_B] * dx * dy + p[F_C] * dy * dy;
-                double power = -0.5 * q;
-                if (power > 0.0) continue;
-                double G = exp(power);
-                double alpha = fmin(0.99, p[F_O] * G);
-                if (alpha < ALPHA_MIN) continue;
-                double testT = T * (1.0 - alpha);
-                if (testT < 1e-4) break;
-                acc_id[m] = vals[k]; acc_T[m] = T; acc_a[m] = alpha; acc_G[m] = G;
-                acc_dx[m] = dx; acc_dy[m] = dy; acc_cap[m] = (p[F_O] * G >= 0.99);
-                ++m;
-                T = testT;
-            }
             size_t pix = (size_t)py * W + px;
             double g[3] = { dL_dimg[pix], dL_dimg[(size_t)W * H + pix], dL_dimg[2 * (size_t)W * H + pix] };
-            for (int k = 0; k < m; ++k) {
-                const double *p = proj + (size_t)ORC_NF * acc_id[k];
-                double behind[3];
-                for (int ch = 0; ch < 3; ++ch) {
-                    double sacc = T * bg[ch];
-                    for (int i = k + 1; i < m; ++i) {
-                        const double *pi = proj + (size_t)ORC_NF * acc_id[i];
-                        sacc += acc_T[i] * acc_a[i] * pi[F_R + ch];
-                    }
-                    behind[ch] = sacc;
-                }
-                double dL_dalpha = 0.0;
-                for (int ch = 0; ch < 3; ++ch) {
-                    g_rgb[3 * (size_t)acc_id[k] + ch] += acc_T[k] * acc_a[k] * g[ch];
-                    dL_dalpha += g[ch] * (acc_T[k] * p[F_R + ch] - behind[ch] / (1.0 - acc_a[k]));
-                }
-                if (acc_cap[k]) continue;
-                double G = acc_G[k], o = p[F_O];
-                g_o[acc_id[k]] += G * dL_dalpha;
-                double dL_dq = dL_dalpha * o * G * (-0.5);
-                double dx = acc_dx[k], dy = acc_dy[k];
-                g_conic[3 * (size_t)acc_id[k] + 0] += dL_dq * dx * dx;
-                g_conic[3 * (size_t)acc_id[k] + 1] += dL_dq * 2.0 * dx * dy;
-                g_conic[3 * (size_t)acc_id[k] + 2] += dL_dq * dy * dy;
-                g_xy[2 * (size_t)acc_id[k] + 0] += dL_dq * 2.0 * (p[F_A] * dx + p[F_B] * dy);
-                g_xy[2 * (size_t)acc_id[k] + 1] += dL_dq * 2.0 * (p[F_B] * dx + p[F_C] * dy);
-            }
+            backward_pixel(px, py, vals + ranges[2 * t], ranges[2 * t + 1] - ranges[2 * t], proj, bg, g, &w,
+                           g_xy, g_conic, g_o, g_rgb);
         }
-    free(acc_id); free(acc_T); free(acc_a); free(acc_G); free(acc_dx); free(acc_dy); free(acc_cap);
+    bwd_scratch_free(&w);
+}
+
+/* The same sums over the m listed pixels (pxs[k], pys[k]) only, with their
+ * loss gradients dL[k][3]; equal to orc_render_backward with dL_dimg zero
+ * at every other pixel. */
+void orc_render_backward_pixels(int W, int H, int m, const int32_t *pxs, const int32_t *pys,
+                                const int64_t *ranges, const int32_t *vals, const double *proj,
+                                const double *bg, const double *dL, double *g_xy, double *g_conic,
+                                double *g_o, double *g_rgb)
+{
+    int tiles_x = (W + ORC_TILE - 1) / ORC_TILE;
+    orc_bwd_scratch w;
+    if (!bwd_scratch_alloc(&w, longest_list(W, H, ranges))) { bwd_scratch_free(&w); return; }
+    for (int k = 0; k < m; ++k) {
+        int px = pxs[k], py = pys[k];
+        int t = (py / ORC_TILE) * tiles_x + px / ORC_TILE;
+        backward_pixel(px, py, vals + ranges[2 * t], ranges[2 * t + 1] - ranges[2 * t], proj, bg, dL + 3 * (size_t)k,
+                       &w, g_xy, g_conic, g_o, g_rgb);
+    }
+    bwd_scratch_free(&w);
 }
 
 /* ------------------------------------------------------------------------ */

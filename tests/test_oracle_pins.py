@@ -605,3 +605,24 @@ def test_render_backward_matches_finite_differences_fp64():
                 assert an == pytest.approx(fd, rel=1e-4, abs=1e-6), (key, i, j, an, fd)
                 checked += 1
     assert checked > 40
+
+
+def test_pixel_subset_backward_equals_the_masked_full_backward():
+    """render_backward_pixels over a pixel subset equals render_backward with
+    dL/dimg zero outside the subset, exactly (the same per-pixel sums in the
+    same order)."""
+    sc, cam = small_scene(n=600, seed=12, W=48, H=40, deg=0)
+    W, H = cam["width"], cam["height"]
+    proj = O.project(sc, cam)
+    L = O.own_lists(proj, W, H)
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((3, H, W))
+    mask = rng.random((H, W)) < 0.3
+    Gm = G * mask
+    full = O.render_backward(W, H, L["ranges"], L["vals"], proj, Gm, bg=(0.1, 0.2, 0.3))
+    pys, pxs = np.nonzero(mask)
+    sub = O.render_backward_pixels(W, H, pxs, pys, G[:, pys, pxs].T, L["ranges"], L["vals"], proj,
+                                   bg=(0.1, 0.2, 0.3))
+    for a, b in zip(full, sub):
+        assert np.any(a != 0)
+        np.testing.assert_array_equal(a, b)
