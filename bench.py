@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--digit-bits", type=int, default=None)
-    ap.add_argument("--sort-mode", default="depth_first", choices=["depth_first", "full_key", "chunked"])
+    ap.add_argument("--sort-mode", default="depth_first", choices=["depth_first", "full_key"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched comparison")
     ap.add_argument("--no-c3", action="store_true", help="skip the 3M-Gaussian zoom sweep")
@@ -173,7 +173,7 @@ def run_ours(args, rank, world, local_rank):
         frames[mode] = R.Frame(n, W, H, cap)
         frames[mode].set_tuning(digit_bits=digit_bits, sort_mode=args.sort_mode)
     # the same QuadBox frame with the other pair-ordering schemes, for comparison
-    other_modes = [m for m in ("depth_first", "chunked", "full_key") if m != args.sort_mode]
+    other_modes = [m for m in ("depth_first", "full_key") if m != args.sort_mode]
     for m in other_modes:
         frames["quadbox_" + m] = R.Frame(n, W, H, int(pairs["quadbox"] * 1.1) + 4096)
         frames["quadbox_" + m].set_tuning(digit_bits=8, sort_mode=m)

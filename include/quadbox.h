@@ -69,22 +69,15 @@ typedef enum {
 } qb_bin_mode;
 #define QB_BIN_NO_CLAMP 0x100
 
-/* How qb_bin_emit/qb_sort order the pairs by (tile, depth, index).  All give
+/* How qb_bin_emit/qb_sort order the pairs by (tile, depth, index).  Both give
  * identical sorted values and ranges.
  *  DEPTH_FIRST  (default) sort the n Gaussians by (depth, index) once, emit
  *               each Gaussian's pairs in that order with 32-bit tile keys, then
  *               stable-sort the pairs on the tile bits only (with emit_fused
  *               the emit runs the first digit pass itself).
  *  FULL_KEY     emit in index order with 64-bit keys (tile << 31) | depth
- *               bits and stable-sort on all 31 + tile bits (SortPairs, Sec. 2).
- *  CHUNKED      depth order as DEPTH_FIRST, then a counting placement instead
- *               of radix passes: per chunk of 65536 depth-ordered pairs the
- *               tile counts come from the QPass segments, their scan over the
- *               chunks gives every (chunk, tile) its first output position, and
- *               each pair is written once, at its final position.  Frames whose
- *               per-tile tables do not fit shared memory (more than about
- *               24000 tiles), and the QUADBOX_NAIVE mode, run DEPTH_FIRST. */
-typedef enum { QB_SORT_DEPTH_FIRST = 0, QB_SORT_FULL_KEY = 1, QB_SORT_CHUNKED = 2 } qb_sort_mode;
+ *               bits and stable-sort on all 31 + tile bits (SortPairs, Sec. 2). */
+typedef enum { QB_SORT_DEPTH_FIRST = 0, QB_SORT_FULL_KEY = 1 } qb_sort_mode;
 
 /* Pinhole camera.  viewmat: row-major 4x4 world->view, last row (0,0,0,1);
  * view space looks down +z.  Pixel (px, py) has its centre at
@@ -153,8 +146,11 @@ typedef struct {
                                  sort's first digit pass (per-tile counts from
                                  the preprocess); 0 (default) = plain emit, the
                                  per-tile counts from a histogram of the
-                                 emitted tile ids in qb_sort; set before
-                                 qb_preprocess                               */
+                                 emitted tile ids in qb_sort.  Frames of more
+                                 than 24576 tiles (beyond the histogram's
+                                 shared memory, e.g. 3840 x 2160) always take
+                                 the fused emit; 1 selects it on any frame.
+                                 Set before qb_preprocess                    */
     int32_t reserved[3];      /* internal */
 } qb_frame;
 
@@ -182,7 +178,14 @@ typedef struct {
     int32_t *n_eval;    /* [H][W]  list entries the pixel evaluated before it
                                    stopped (render statistics)               */
     uint64_t *n_pairs;  /* [1]     P on the device                          */
-    uint32_t *err_flags;/* [1]     bit0 capacity, bit1 timeout              */
+    uint32_t *err_flags;/* [2]     [0]: bit0 capacity, bit1 timeout.  [1]:
+                                   test-only, zero after qb_frame_init; a test
+                                   may set it to k > 0 to exercise a bounded
+                                   spin-wait: the second block of the last
+                                   (values-only) tile-sort pass then finds its
+                                   predecessor unpublished, gives up after k
+                                   polls and raises TIMEOUT; the sorted values
+                                   are then undefined (do not render them)  */
 } qb_frame_arrays;
 
 /* Thread-local description of the last failure. */
@@ -396,8 +399,9 @@ qb_status qb_batch_check(qb_batch *batch, uint64_t *pairs_out, qb_stream_t strea
  * frees memory.  Sizes whose scratch (qb_sort_scratch_bytes(n, end_bit,
  * digit_bits) minus 256) exceeds that array are rejected with INVALID_ARG,
  * e.g. more than about 11M pairs at 44 key bits with 8-bit digits.
- * Arguments and result as for qb_sort_pairs.  The first call on a device
- * looks up the array's device address; make it before any stream capture.
+ * Arguments and result as for qb_sort_pairs.  Every call looks up the
+ * array's device address on the current device (the first call on a device
+ * may load the library's device code; make it before any stream capture).
  * All calls share the one array, and each call clears what must start at
  * zero, so calls whose work overlaps on the GPU (other streams, other host
  * threads) race with each other: serialise them.  Synchronises the stream

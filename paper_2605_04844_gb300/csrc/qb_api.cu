@@ -58,7 +58,6 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     L.counts = take(4 * N);
     L.offsets = take(4 * N);
     L.segs = take(64 * N);
-    L.segs_d = take(64 * N);
     L.scan_part = take(8 * scan_partials_count(n));
     L.keys0 = take(8 * cap);
     L.keys1 = take(8 * cap);
@@ -82,11 +81,7 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     }
     L.dsort_scratch = take(db);
     L.ranges = take(8 * (size_t)tiles);
-    const uint64_t n_chunks = (cap + kChunkPairs - 1) / kChunkPairs + 1;
-    L.chunk_start = take(4 * (n_chunks + 1));
-    L.chunk_cnt = take(4 * n_chunks * (size_t)tiles);
-    L.chunk_part = take(4 * (size_t)kChunkSegs * tiles);
-    L.chunk_total = take(4 * ((size_t)tiles + 1));  // + the tile histogram's block counter
+    L.tile_counts = take(4 * ((size_t)tiles + 1));  // + the tile histogram's block counter
     L.tile_diff = take(4 * (size_t)(tx + 1) * (ty + 1));
     L.tile_single = take(4 * (size_t)tiles);
     L.tfinal = take(4 * (size_t)W * H);
@@ -149,15 +144,6 @@ qb_status check_frame(const qb_frame *f, Layout &L) {
     if (!make_layout(f->n, f->width, f->height, f->pair_capacity, L))
         return fail(QB_ERR_INVALID_ARG, "frame has invalid sizes");
     return QB_OK;
-}
-
-// The sort a frame actually runs: QB_SORT_CHUNKED falls back to the radix
-// tile sort for the naive traversal (whose emit is the nested-loop one) and
-// for images whose per-tile tables exceed the kernels' shared memory.
-int effective_sort(const qb_frame *f, int base_mode) {
-    if (f->sort_mode != QB_SORT_CHUNKED) return f->sort_mode;
-    if (base_mode == QB_BIN_QUADBOX_NAIVE || !chunked_smem_ok(f->tiles_x, f->tiles_y)) return QB_SORT_DEPTH_FIRST;
-    return QB_SORT_CHUNKED;
 }
 
 qb_status check_scene(const qb_frame *f, const qb_scene *s) {
@@ -344,9 +330,9 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     a.segs = at<uint4>(frame, L.segs);
     std::memset(a.diff_off, 0, sizeof(a.diff_off));
     std::memset(a.single_off, 0, sizeof(a.single_off));
-    if (frame->sort_mode < QB_SORT_DEPTH_FIRST || frame->sort_mode > QB_SORT_CHUNKED)
+    if (frame->sort_mode < QB_SORT_DEPTH_FIRST || frame->sort_mode > QB_SORT_FULL_KEY)
         return fail(QB_ERR_INVALID_ARG, "invalid sort_mode %d", frame->sort_mode);
-    const int eff = effective_sort(frame, base_mode);
+    const int eff = frame->sort_mode;
     // the fused emit needs the per-tile counts before it runs: from the
     // preprocess's difference arrays (also when the grid is too large for the
     // histogram of the unfused path)
@@ -378,7 +364,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     qb_status st = check_frame(frame, L);
     if (st != QB_OK) return st;
     if (frame->stage < 1) return fail(QB_ERR_STATE, "qb_bin_emit before qb_preprocess");
-    if (frame->sort_mode < QB_SORT_DEPTH_FIRST || frame->sort_mode > QB_SORT_CHUNKED)
+    if (frame->sort_mode < QB_SORT_DEPTH_FIRST || frame->sort_mode > QB_SORT_FULL_KEY)
         return fail(QB_ERR_INVALID_ARG, "invalid sort_mode %d", frame->sort_mode);
     if (frame->sort_mode != (frame->reserved[0] & 0xff))
         return fail(QB_ERR_STATE, "sort_mode changed between qb_preprocess and qb_bin_emit");
@@ -450,36 +436,7 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     a.clamp3s = (frame->bin_mode & QB_BIN_NO_CLAMP) == 0;
     a.err = err;
     a.segs = at<uint4>(frame, L.segs);
-    if (eff == QB_SORT_CHUNKED) {
-        // per-chunk tile counts, their scan (and the ranges), placement
-        const uint64_t n_max = frame->n_pairs != UINT64_MAX ? frame->n_pairs : frame->pair_capacity;
-        ChunkArgs c;
-        std::memset(&c, 0, sizeof(c));
-        c.tiles_x = frame->tiles_x;
-        c.tiles_y = frame->tiles_y;
-        chunked_bands(c.tiles_x, c.tiles_y, c.band_rows, c.n_bands);
-        c.band_diff_ints = (c.band_rows + 1) * (c.tiles_x + 1);
-        c.band_words = (c.band_rows * c.tiles_x + 3) & ~3;
-        c.chunk_pairs = kChunkPairs;
-        c.n_chunks = (uint32_t)((n_max + kChunkPairs - 1) / kChunkPairs);
-        if (c.n_chunks == 0) c.n_chunks = 1;
-        c.n_segs = kChunkSegs;
-        c.chunks_per_seg = (c.n_chunks + kChunkSegs - 1) / kChunkSegs;
-        c.perm = perm;
-        c.counts = a.counts;
-        c.segs = a.segs;
-        c.segs_d = at<uint4>(frame, L.segs_d);
-        c.n_pairs = d_np;
-        c.capacity = frame->pair_capacity;
-        c.start = at<uint32_t>(frame, L.chunk_start);
-        c.cnt = at<uint32_t>(frame, L.chunk_cnt);
-        c.part = at<uint32_t>(frame, L.chunk_part);
-        c.total = at<uint32_t>(frame, L.chunk_total);
-        a.vals = at<uint32_t>(frame, L.vals0);
-        QB_CUDA(launch_chunked(a, c, at<uint2>(frame, L.ranges), s));
-        frame->reserved[1] = frame->sort_digit_bits;
-        frame->reserved[2] = 0;
-    } else if (depth_first) {
+    if (depth_first) {
         // QPass emit in depth order; in the QPass modes it also performs the
         // tile sort's first digit pass (qb_sort runs the remaining ones)
         void *scratch = at<void>(frame, L.sort_scratch);
@@ -527,9 +484,7 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
     uint32_t *err = at<uint32_t>(frame, L.state + 8);
     const int eff = (frame->reserved[0] >> 8) & 0xff;
     const bool fused = (frame->reserved[0] >> 16) & 1;
-    if (eff == QB_SORT_CHUNKED) {
-        frame->sorted_in_alt = 0;  // qb_bin_emit placed the values in their sorted positions
-    } else if (eff == QB_SORT_DEPTH_FIRST) {
+    if (eff == QB_SORT_DEPTH_FIRST) {
         // pairs were emitted in depth order: a stable sort on the tile id alone
         // (bucket offsets and ranges came from the per-tile counts in qb_bin_emit)
         if (frame->sort_digit_bits != frame->reserved[1])
@@ -541,7 +496,7 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
             // per-tile counts from the emitted tile ids -> ranges and every
             // pass's bucket offsets
             const uint32_t *src = at<uint32_t>(frame, passes > 0 && pass_writes_a(passes, 0) ? L.keys1 : L.keys0);
-            uint32_t *counts = at<uint32_t>(frame, L.chunk_total);
+            uint32_t *counts = at<uint32_t>(frame, L.tile_counts);
             QB_CUDA(launch_tile_count(src, n_max, n_dev, ntiles, counts, at<uint2>(frame, L.ranges),
                                       sort_hist_table(at<void>(frame, L.sort_scratch)), sort_hist_stride(), rb,
                                       tile_bits, s));
@@ -688,7 +643,8 @@ qb_status qb_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_keys_alt
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *base = static_cast<uint8_t *>(d_scratch);
     uint32_t *err = reinterpret_cast<uint32_t *>(base + need - 256);
-    QB_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    // the error word and the test-only word after it (qb_sweep.cuh) start at zero
+    QB_CUDA(cudaMemsetAsync(err, 0, 8, s));
     int passes = 0;
     QB_CUDA(sort_pairs(d_keys, d_vals, d_keys_alt, d_vals_alt, n, nullptr, end_bit, digit_bits, d_scratch, err, s,
                        &passes));

@@ -600,391 +600,6 @@ cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_de
     return cudaGetLastError();
 }
 
-// ---- chunked counting placement (QB_SORT_CHUNKED) ---------------------------
-// The depth-ordered pair stream is cut into chunks of Gaussians whose first
-// pairs fall in [c K, (c+1) K).  Per chunk and tile the pairs are counted
-// from the Gaussians' QPass segments with a 2D difference array in shared
-// memory; an exclusive scan of the counts over the chunks (per tile, plus the
-// tile ranges) gives every (chunk, tile) its first output position; and one
-// warp per chunk walks its pairs in order and places each at its tile's
-// running position.  Pairs of one tile thus keep the emission (depth, index)
-// order, which is exactly the stable sort by tile of the depth-ordered pairs.
-
-// start[c] = first emission position j with offsets[j] >= min(c K, P): the
-// Gaussians without tiles (all at the end of the depth order, offset P) fall
-// in no chunk.
-__global__ void chunk_start_kernel(const uint32_t *__restrict__ offsets, int n, uint32_t n_chunks, uint32_t K,
-                                   const uint64_t *n_pairs, uint32_t *start) {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > n_chunks) return;
-    const uint64_t P = *n_pairs;
-    const uint64_t target = (uint64_t)c * K < P ? (uint64_t)c * K : P;
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((uint64_t)offsets[mid] < target) lo = mid + 1;
-        else hi = mid;
-    }
-    start[c] = (uint32_t)lo;
-}
-
-// A chunk is processed in bands of tile rows, one warp per (chunk, band):
-// a band's tables fit a few KB of shared memory, so many warps run per SM.
-
-// The segments of one record (src, whose first uint4 c0 the caller has
-// loaded) clipped to tile rows [y0, y1), in fixed slots (empty ones zero; ns
-// counts the others); returns their pair count (0 when the Gaussian misses
-// the band).
-
-// Records in emission order, for the chunk tasks' contiguous reads.
-__global__ void chunk_gather_kernel(ChunkArgs a, int n) {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= (uint32_t)n || j >= a.start[a.n_chunks]) return;  // Gaussians without tiles are never read
-    const uint4 *src = a.segs + 4 * (size_t)a.perm[j];
-    uint4 *dst = a.segs_d + 4 * (size_t)j;
-    const uint4 c0 = src[0];
-    dst[0] = c0;
-    const int nc = seg_chunks((int)(c0.x & 7u));
-    for (int q = 1; q < nc; ++q) dst[q] = src[q];
-}
-
-__device__ __forceinline__ uint32_t band_segments(const uint4 *__restrict__ src, uint4 c0, int y0, int y1,
-                                                  QSeg seg[7], int &ns, bool &columns) {
-    ns = 0;
-    columns = false;
-    const int ylo = (int)((c0.x >> 4) & 0x3fffu), yhi = (int)((c0.x >> 18) & 0x3fffu);
-    if (yhi < y0 || ylo >= y1) {
-#pragma unroll
-        for (int q = 0; q < 7; ++q) seg[q] = QSeg{0, 0, 0, 0};
-        return 0u;
-    }
-    const int n_in = (int)(c0.x & 7u);
-    columns = (c0.x >> 3) & 1u;
-    uint32_t w[16];
-    w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
-    const int nc = seg_chunks(n_in);
-#pragma unroll
-    for (int q = 1; q < 4; ++q) {
-        const uint4 v = q < nc ? src[q] : make_uint4(0u, 0u, 0u, 0u);
-        w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
-    }
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        seg[q] = QSeg{0, 0, 0, 0};
-        if (q >= n_in) continue;
-        int s0 = (int)(w[1 + 2 * q] & 0xffffu), lo = (int)(w[1 + 2 * q] >> 16);
-        int nl = (int)(w[2 + 2 * q] & 0xffffu), len = (int)(w[2 + 2 * q] >> 16);
-        if (columns) {  // lines are columns: clip the interval (rows)
-            const int a = max(lo, y0), b = min(lo + len, y1);
-            lo = a;
-            len = b - a;
-        } else {  // lines are rows: clip the lines
-            const int a = max(s0, y0), b = min(s0 + nl, y1);
-            s0 = a;
-            nl = b - a;
-        }
-        if (nl <= 0 || len <= 0) continue;
-        seg[q] = QSeg{s0, lo, nl, len};
-        ++ns;
-        cnt += (uint32_t)(nl * len);
-    }
-    return cnt;
-}
-
-// Per (chunk, band): the band's tile counts cnt[c][t] from a 2D difference
-// array of the clipped segments.  Four warps (bands) per block.
-constexpr int kBandWarps = 4;
-
-__global__ void __launch_bounds__(kBandWarps * 32) chunk_count_kernel(ChunkArgs a) {
-    extern __shared__ int s_diff[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int band = blockIdx.x * kBandWarps + wid;
-    const uint32_t c = blockIdx.y;
-    if (band >= a.n_bands) return;  // warp-uniform; only warp-level syncs below
-    const int tx = a.tiles_x, T = tx * a.tiles_y, stride = tx + 1;
-    const int y0 = band * a.band_rows, y1 = min(a.tiles_y, y0 + a.band_rows), rows = y1 - y0;
-    int *D = s_diff + wid * a.band_diff_ints;
-    for (int k = lane; k < (rows + 1) * stride; k += 32) D[k] = 0;
-    __syncwarp();
-    if (*a.n_pairs > a.capacity) return;  // flagged by the emit
-    const uint32_t j0 = a.start[c], j1 = a.start[c + 1];
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    uint4 h = j0 + lane < j1 ? a.segs_d[4 * (size_t)(j0 + lane)] : zero4;
-    for (uint32_t j = j0 + lane; j < j1; j += 32) {
-        const uint4 hc = h;
-        h = j + 32 < j1 ? a.segs_d[4 * (size_t)(j + 32)] : zero4;  // next record's header, early
-        QSeg seg[7];
-        int ns;
-        bool columns;
-        if (band_segments(a.segs_d + 4 * (size_t)j, hc, y0, y1, seg, ns, columns) == 0u) continue;
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            if (seg_empty(seg[q])) continue;
-            const int l0 = seg[q].s0, l1 = seg[q].s0 + seg[q].nl - 1;
-            const int u0 = seg[q].lo, u1 = seg[q].lo + seg[q].len - 1;
-            const int x0 = columns ? l0 : u0, x1 = columns ? l1 : u1;
-            const int ya = (columns ? u0 : l0) - y0, yb = (columns ? u1 : l1) - y0;
-            atomicAdd(D + ya * stride + x0, 1);
-            atomicAdd(D + ya * stride + x1 + 1, -1);
-            atomicAdd(D + (yb + 1) * stride + x0, -1);
-            atomicAdd(D + (yb + 1) * stride + x1 + 1, 1);
-        }
-    }
-    __syncwarp();
-    for (int r = 0; r < rows; ++r) {  // prefix along x
-        int carry = 0;
-        for (int x0 = 0; x0 < tx; x0 += 32) {
-            const int x = x0 + lane;
-            const int v = x < tx ? D[r * stride + x] : 0;
-            const int incl = warp_incl_scan(v) + carry;
-            if (x < tx) D[r * stride + x] = incl;
-            carry = __shfl_sync(0xffffffffu, incl, 31);
-        }
-    }
-    __syncwarp();
-    uint32_t *row = a.cnt + (size_t)c * T + (size_t)y0 * tx;
-    for (int x = lane; x < tx; x += 32) {  // prefix along y, and out
-        int run = 0;
-        for (int r = 0; r < rows; ++r) {
-            run += D[r * stride + x];
-            row[r * tx + x] = (uint32_t)run;
-        }
-    }
-}
-
-// part[s][t] = sum of cnt[c][t] over the chunks of segment s.
-__global__ void chunk_part_kernel(ChunkArgs a) {
-    const int T = a.tiles_x * a.tiles_y;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    const uint32_t s = blockIdx.y;
-    const uint32_t c0 = s * a.chunks_per_seg, c1 = min(c0 + a.chunks_per_seg, a.n_chunks);
-    uint32_t sum = 0;
-#pragma unroll 8
-    for (uint32_t c = c0; c < c1; ++c) sum += a.cnt[(size_t)c * T + t];
-    a.part[(size_t)s * T + t] = sum;
-}
-
-// Per tile: exclusive scan of part over the chunk segments, and the tile's
-// total.
-__global__ void chunk_tile_scan_kernel(ChunkArgs a) {
-    const int T = a.tiles_x * a.tiles_y;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    uint32_t v[kChunkSegs];
-#pragma unroll
-    for (uint32_t q = 0; q < kChunkSegs; ++q) v[q] = q < a.n_segs ? a.part[(size_t)q * T + t] : 0u;
-    uint32_t run = 0;
-#pragma unroll
-    for (uint32_t q = 0; q < kChunkSegs; ++q) {
-        if (q < a.n_segs) a.part[(size_t)q * T + t] = run;
-        run += v[q];
-    }
-    a.total[t] = run;
-}
-
-// The ranges: exclusive scan of the tile totals over the tiles (one block);
-// total[t] becomes the tile's first position.
-__global__ void __launch_bounds__(1024) chunk_ranges_kernel(ChunkArgs a, uint2 *ranges) {
-    const int T = a.tiles_x * a.tiles_y;
-    const int per = (T + blockDim.x - 1) / blockDim.x;
-    const int t0 = threadIdx.x * per, t1 = min(T, t0 + per);
-    uint64_t local64 = 0;
-    for (int t = t0; t < t1; ++t) local64 += a.total[t];
-    uint64_t total64;
-    block_incl_scan<uint64_t>(local64, &total64);
-    // more pairs than the buffers hold: the count kernel wrote no table, the
-    // emit writes nothing, and every tile is left empty
-    const bool over = *a.n_pairs > a.capacity || total64 > a.capacity;
-    uint32_t local = over ? 0u : (uint32_t)local64;
-    uint32_t tot;
-    uint32_t run = block_incl_scan<uint32_t>(local, &tot) - local;
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t v = over ? 0u : a.total[t];
-        ranges[t] = v ? make_uint2(run, run + v) : make_uint2(0u, 0u);
-        a.total[t] = run;
-        run += v;
-    }
-}
-
-// cnt[c][t] <- first output position of chunk c's pairs in tile t.
-__global__ void chunk_base_kernel(ChunkArgs a) {
-    const int T = a.tiles_x * a.tiles_y;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    const uint32_t s = blockIdx.y;
-    const uint32_t c0 = s * a.chunks_per_seg, c1 = min(c0 + a.chunks_per_seg, a.n_chunks);
-    uint32_t run = a.total[t] + a.part[(size_t)s * T + t];
-    for (uint32_t cb = c0; cb < c1; cb += 8) {
-        uint32_t v[8];  // loads first, then the stores (they cannot alias)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = cb + k < c1 ? a.cnt[(size_t)(cb + k) * T + t] : 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (cb + k < c1) a.cnt[(size_t)(cb + k) * T + t] = run;
-            run += v[k];
-        }
-    }
-}
-
-// Per (chunk, band): the chunk's Gaussians in emission order, their pairs in
-// the band generated 32 at a time (QPass segments, as in emit_range), and each
-// pair written at its tile's running position.  Lanes of a group of 32 that
-// share a tile are found with one ballot per tile-id bit that varies in the
-// group, and ranked in lane (emission) order.
-__global__ void __launch_bounds__(kBandWarps * 32) chunk_emit_kernel(EmitArgs e, ChunkArgs a) {
-    extern __shared__ __align__(16) uint8_t s_band[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int band = blockIdx.x * kBandWarps + wid;
-    const uint32_t c = blockIdx.y;
-    const uint64_t P = *e.n_pairs;
-    if (P > e.capacity) {
-        if (c == 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(e.err, kErrCapacity);
-        return;
-    }
-    if (band >= a.n_bands) return;  // warp-uniform
-    const int tx = a.tiles_x, T = tx * a.tiles_y;
-    const int y0 = band * a.band_rows, y1 = min(a.tiles_y, y0 + a.band_rows);
-    const uint32_t t0 = (uint32_t)y0 * tx, nb = (uint32_t)(y1 - y0) * tx;
-    uint8_t *mine = s_band + (size_t)wid * ((size_t)a.band_words * 4 + sizeof(SegTable));
-    uint32_t *cursor = reinterpret_cast<uint32_t *>(mine);
-    SegTable &S = *reinterpret_cast<SegTable *>(mine + (size_t)a.band_words * 4);
-    const uint32_t j0 = a.start[c], j1 = a.start[c + 1];
-    if (j0 >= j1) return;
-    const uint32_t *row = a.cnt + (size_t)c * T + t0;
-    for (uint32_t k = lane; k < nb; k += 32) cursor[k] = row[k];
-    __syncwarp();
-    uint32_t *vals = e.vals;
-    const uint64_t cap = e.capacity;
-    const uint32_t lt = lanemask_lt(), le_mask = lanemask_le();
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    uint4 h = j0 + lane < j1 ? a.segs_d[4 * (size_t)(j0 + lane)] : zero4;
-    uint32_t gn = j0 + lane < j1 ? a.perm[j0 + lane] : 0u;
-    for (uint32_t jb = j0; jb < j1; jb += 32) {
-        const uint32_t j = jb + lane;
-        const uint4 hc = h;
-        const uint32_t g = gn;
-        if (j + 32 < j1) {  // the next batch's header and index, early
-            h = a.segs_d[4 * (size_t)(j + 32)];
-            gn = a.perm[j + 32];
-        }
-        QSeg seg[7];
-        int ns = 0;
-        bool columns = false;
-        uint32_t cnt = 0u;
-        if (j < j1) cnt = band_segments(a.segs_d + 4 * (size_t)j, hc, y0, y1, seg, ns, columns);
-        const uint32_t incl = warp_incl_scan(cnt);
-        const uint32_t btotal = __shfl_sync(0xffffffffu, incl, 31);
-        if (btotal == 0u) continue;  // warp-uniform
-        const int sincl = warp_incl_scan(ns);
-        const int nseg = __shfl_sync(0xffffffffu, sincl, 31);
-        __syncwarp();
-        S.gid[lane] = g;
-        int32_t r0 = (int32_t)(incl - cnt);
-        int k = sincl - ns;
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            if (seg_empty(seg[q])) continue;
-            S.start[k] = r0;
-            S.geo[k] = (uint32_t)seg[q].s0 | ((uint32_t)seg[q].lo << 16);
-            S.len[k] = (uint32_t)seg[q].len | ((uint32_t)lane << 16) | ((uint32_t)columns << 24);
-            S.inv[k] = 1.0f / (float)seg[q].len;
-            r0 += seg[q].nl * seg[q].len;
-            ++k;
-        }
-        __syncwarp();
-        int cur = -1;  // last segment starting at or before the group's first position
-        for (int32_t c0 = 0; c0 < (int32_t)btotal; c0 += 32) {
-            const int cand = cur + 1 + lane;
-            uint32_t bit = 0u;
-            if (cand < nseg) {
-                const int32_t st = S.start[cand];
-                if (st < c0 + 32) bit = 1u << (st - c0);
-            }
-            const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
-            const int32_t p = c0 + lane;
-            const bool valid = p < (int32_t)btotal;
-            uint32_t key = 4096u + (uint32_t)lane, gid = 0u;  // invalid lanes: keys no band tile has
-            if (valid) {
-                const int idx = cur + __popc(M & le_mask);
-                const int32_t st = S.start[idx];
-                const uint32_t geo = S.geo[idx], ln = S.len[idx];
-                const uint32_t k = (uint32_t)(p - st), len = ln & 0xffffu;
-                int32_t q = (int32_t)((float)k * S.inv[idx]);
-                int32_t r = (int32_t)k - q * (int32_t)len;
-                if (r < 0) { --q; r += (int32_t)len; }
-                if (r >= (int32_t)len) { ++q; r -= (int32_t)len; }
-                const uint32_t line = (geo & 0xffffu) + (uint32_t)q;
-                const uint32_t u = (geo >> 16) + (uint32_t)r;
-                const bool cols = (ln >> 24) & 1u;
-                const uint32_t tile = (cols ? u : line) * (uint32_t)tx + (cols ? line : u);
-                key = tile - t0;
-                gid = S.gid[(ln >> 16) & 0xffu];
-            }
-            cur += __popc(M);
-            // lanes with the same key: one ballot per varying key bit
-            const uint32_t vary = __reduce_or_sync(0xffffffffu, key) ^ __reduce_and_sync(0xffffffffu, key);
-            uint32_t peers = 0xffffffffu, vb = vary;
-            while (vb) {
-                const int b = __ffs(vb) - 1;
-                vb &= vb - 1u;
-                const bool set = (key >> b) & 1u;
-                const uint32_t bb = __ballot_sync(0xffffffffu, set);
-                peers &= set ? bb : ~bb;
-            }
-            const uint32_t rank = __popc(peers & lt);
-            uint32_t base = 0u;
-            if (valid && rank == 0u) {
-                base = cursor[key];
-                cursor[key] = base + (uint32_t)__popc(peers);
-            }
-            base = __shfl_sync(0xffffffffu, base, __ffs(peers) - 1);
-            const uint64_t pos = (uint64_t)base + rank;
-            if (valid && pos < cap) vals[pos] = gid;
-            __syncwarp();
-        }
-    }
-}
-
-cudaError_t launch_chunked(const EmitArgs &e, const ChunkArgs &a, uint2 *ranges, cudaStream_t s) {
-    const int T = a.tiles_x * a.tiles_y;
-    if (e.n == 0 || T == 0) return cudaSuccess;
-    note_launch("chunk_start_kernel", s), chunk_start_kernel<<<(a.n_chunks + 1 + 255) / 256, 256, 0, s>>>(e.offsets, e.n, a.n_chunks,
-                                                                                a.chunk_pairs, e.n_pairs, a.start);
-    const size_t smem_count = (size_t)kBandWarps * a.band_diff_ints * 4;
-    const size_t smem_emit = (size_t)kBandWarps * ((size_t)a.band_words * 4 + sizeof(SegTable));
-    cudaError_t err;
-    if ((err = ensure_dyn_smem((const void *)chunk_count_kernel, smem_count)) != cudaSuccess) return err;
-    if ((err = ensure_dyn_smem((const void *)chunk_emit_kernel, smem_emit)) != cudaSuccess) return err;
-    note_launch("chunk_gather_kernel", s), chunk_gather_kernel<<<(e.n + 255) / 256, 256, 0, s>>>(a, e.n);
-    const dim3 bg((a.n_bands + kBandWarps - 1) / kBandWarps, a.n_chunks);
-    note_launch("chunk_count_kernel", s), chunk_count_kernel<<<bg, kBandWarps * 32, smem_count, s>>>(a);
-    const dim3 tg((T + 255) / 256, a.n_segs);
-    note_launch("chunk_part_kernel", s), chunk_part_kernel<<<tg, 256, 0, s>>>(a);
-    note_launch("chunk_tile_scan_kernel", s), chunk_tile_scan_kernel<<<(T + 255) / 256, 256, 0, s>>>(a);
-    note_launch("chunk_ranges_kernel", s), chunk_ranges_kernel<<<1, 1024, 0, s>>>(a, ranges);
-    note_launch("chunk_base_kernel", s), chunk_base_kernel<<<tg, 256, 0, s>>>(a);
-    note_launch("chunk_emit_kernel", s), chunk_emit_kernel<<<bg, kBandWarps * 32, smem_emit, s>>>(e, a);
-    return cudaGetLastError();
-}
-
-// Band geometry of the chunked placement for a tiles_x x tiles_y grid: rows
-// per band such that a band has at most kBandTiles tiles.  False when a single
-// row is wider than that or the grid is too tall for the segment records.
-bool chunked_bands(int tiles_x, int tiles_y, int &band_rows, int &n_bands) {
-    if (tiles_x <= 0 || tiles_y <= 0 || tiles_x > kBandTiles || tiles_y >= (1 << 14)) return false;
-    band_rows = kBandTiles / tiles_x;
-    if (band_rows > 8) band_rows = 8;  // more bands, more warps
-    n_bands = (tiles_y + band_rows - 1) / band_rows;
-    return true;
-}
-
-bool chunked_smem_ok(int tiles_x, int tiles_y) {
-    int r, b;
-    return chunked_bands(tiles_x, tiles_y, r, b);
-}
-
 // The tile id of every sorted pair position, from the ranges (one block per
 // tile).
 // Positions at or beyond n_out are not written.

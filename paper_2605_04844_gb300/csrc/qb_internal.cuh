@@ -38,13 +38,13 @@ struct CamDev {
 
 // Workspace offsets (bytes) of a frame; all 256-byte aligned.
 struct Layout {
-    size_t xy, conic_o, rgbd, box, r3, meta, counts, offsets, segs, segs_d;
+    size_t xy, conic_o, rgbd, box, r3, meta, counts, offsets, segs;
     size_t scan_part;
     size_t keys0, keys1, vals0, vals1;
     size_t sort_scratch, sort_scratch_bytes;
     size_t dkeys0, dkeys1, dvals0, dvals1, dsort_scratch;  // depth order of the Gaussians
     size_t ranges, tfinal, ncontrib, neval;
-    size_t chunk_start, chunk_cnt, chunk_part, chunk_total;  // chunked placement tables
+    size_t tile_counts;  // per-tile pair counts of the tile histogram (+ its block counter)
     size_t tile_diff;  // (tiles_y+1) x (tiles_x+1) int difference array
     size_t tile_single;  // tiles ints: pair counts of single-tile Gaussians
     size_t gscreen;  // [n][9] screen-space gradients

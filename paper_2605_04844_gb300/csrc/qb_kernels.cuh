@@ -90,31 +90,6 @@ struct EmitArgs {
     TileSet ts;  // camera of record r is r / n_per_cam
 };
 
-// Chunked counting placement of the depth-ordered pairs (one camera).
-constexpr uint32_t kChunkPairs = 65536;     // pairs per chunk (K)
-constexpr uint32_t kChunkSegs = 32;         // chunk segments of the two-level scan
-constexpr size_t kChunkMaxSmem = 96 * 1024;  // shared memory bound of its kernels
-
-constexpr int kBandTiles = 4096;  // tiles of one band at most (band-local keys < 2^12)
-
-struct ChunkArgs {
-    int tiles_x, tiles_y;
-    int band_rows, n_bands;  // tile rows per band, bands
-    int band_diff_ints;      // (band_rows + 1) x (tiles_x + 1)
-    int band_words;          // per-warp shared words of the placement: cursor (band tiles, rounded to 4)
-    uint32_t n_chunks, chunk_pairs, n_segs, chunks_per_seg;
-    const uint32_t *perm;    // emission order -> Gaussian
-    const uint32_t *counts;  // by Gaussian
-    const uint4 *segs;       // QPass segment records by Gaussian
-    uint4 *segs_d;           // the same records in emission (depth) order
-    const uint64_t *n_pairs;
-    uint64_t capacity;
-    uint32_t *start;  // [n_chunks + 1]
-    uint32_t *cnt;    // [n_chunks][tiles]: counts, then first positions
-    uint32_t *part;   // [n_segs][tiles]
-    uint32_t *total;  // [tiles]
-};
-
 struct RenderArgs {
     const uint2 *ranges;  // by global tile
     const uint32_t *vals;
@@ -172,9 +147,6 @@ cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s);
 cudaError_t launch_emit_sweep(const EmitArgs &a, int digit_bits, bool write_keys, uint32_t *kout, uint32_t *vout,
                               const uint32_t *bin_off, uint32_t *lookback, uint32_t *counter, cudaStream_t s);
 // Counts, scans and places the pairs (writes e.vals and the ranges).
-cudaError_t launch_chunked(const EmitArgs &e, const ChunkArgs &a, uint2 *ranges, cudaStream_t s);
-bool chunked_smem_ok(int tiles_x, int tiles_y);
-bool chunked_bands(int tiles_x, int tiles_y, int &band_rows, int &n_bands);
 cudaError_t launch_expand_ranges(const uint2 *ranges, int ntiles, uint32_t *out, uint64_t n_out, cudaStream_t s);
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, uint64_t n_max, const uint64_t *n_dev, uint2 *ranges, int ntiles,

@@ -10,7 +10,6 @@
 // caller-supplied buffer.  The array is part of the library image, so every
 // GPU that loads the library holds it until the process exits.
 #include <cstdio>
-#include <mutex>
 
 #include "qb_kernels.cuh"
 
@@ -21,31 +20,20 @@ constexpr size_t kNoAllocErrOffset = kNoAllocScratchBytes;  // then one 256-byte
 
 __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes + 256];
 
-constexpr int kMaxDevices = 64;
-void *g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
-std::mutex g_noalloc_mu;
-
 qb_status noalloc_fail(qb_status s, const char *msg) {
     qb::set_last_error(msg);
     return s;
 }
 
-// Looks the array's device address up once per device, with that device
-// current.  In host code the symbol name is only a host-side stand-in, so
-// the kernels must be given this address instead.
+// The array's device address on the current device.  In host code the
+// symbol name is only a host-side stand-in, so the kernels must be given this
+// address instead.  It is looked up on every call (a cheap query once the
+// module is loaded), so nothing stale survives a cudaDeviceReset.
 cudaError_t noalloc_scratch(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -80,9 +68,10 @@ qb_status qb_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_
     if (e != cudaSuccess) return noalloc_fail(QB_ERR_CUDA, cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(base) + kNoAllocErrOffset);
-    // the array keeps the previous call's contents: the error word is cleared
-    // here, and sort_pairs clears the histograms, counters and look-back words
-    e = cudaMemsetAsync(err, 0, 4, s);
+    // the array keeps the previous call's contents: the error word and the
+    // test-only word after it are cleared here, and sort_pairs clears the
+    // histograms, counters and look-back words
+    e = cudaMemsetAsync(err, 0, 8, s);
     if (e != cudaSuccess) return noalloc_fail(QB_ERR_CUDA, cudaGetErrorString(e));
     int passes = 0;
     e = qb::sort_pairs(d_keys, d_vals, d_keys_alt, d_vals_alt, n, nullptr, end_bit, digit_bits, base, err, s,

@@ -46,6 +46,17 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// The error word err[0] is followed by a test-only word, zero in normal use:
+// when err[1] > 0, the block of tile 1 of every values-only pass (the last
+// pass of a tile sort, whose output only the render reads) finds tile 0's
+// status words unpublished and gives up after err[1] polls, so its wait runs
+// out deterministically and raises kErrTimeout.  Its scatter positions then
+// fall short of the true ones but stay inside [0, n); the sorted values are
+// undefined.  Other waits keep the kSpinLimit bound.
+__device__ __forceinline__ uint32_t stall_test(const uint32_t *err, uint32_t tile) {
+    return tile == 1 ? ld_relaxed(err + 1) : 0u;
+}
+
 // Elements to sort: the device count when given, treated as zero when it
 // exceeds the buffers (an overflow the emit has already flagged).
 __device__ __forceinline__ uint64_t device_count(const uint64_t *n_dev, uint64_t n_max) {
@@ -203,11 +214,14 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
             int64_t t = (int64_t)tile - 1;
             int spins = 0;
             bool done = false;
+            // test-only (values-only passes): tile 0 reads as unpublished
+            const uint32_t stall = WRITE_KEYS ? 0u : stall_test(err, tile);
             while (!done && t >= 0) {
                 uint32_t sv[kLookWindow];
 #pragma unroll
                 for (int w = 0; w < kLookWindow; ++w)
-                    sv[w] = (t - w >= 0) ? ld_relaxed(lookback + (size_t)(t - w) * R + d) : kFlagIncl;
+                    sv[w] = (t - w >= 0) ? (stall && t - w == 0 ? 0u : ld_relaxed(lookback + (size_t)(t - w) * R + d))
+                                         : kFlagIncl;
                 int used = 0;
 #pragma unroll
                 for (int w = 0; w < kLookWindow; ++w) {
@@ -222,12 +236,13 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
                 if (!done && used == 0) {
                     // the nearest earlier tile has not published this digit yet
                     unsigned ns = 32;
-                    while ((ld_relaxed(lookback + (size_t)t * R + d) & ~kCountMask) == 0u) {
-                        if (++spins > kSpinLimit) break;
+                    const int limit = stall ? (int)min(stall, (uint32_t)kSpinLimit) : kSpinLimit;
+                    while (((stall && t == 0 ? 0u : ld_relaxed(lookback + (size_t)t * R + d)) & ~kCountMask) == 0u) {
+                        if (++spins > limit) break;
                         __nanosleep(ns);
                         ns = ns < 512 ? 2 * ns : 512;
                     }
-                    if (spins > kSpinLimit) {
+                    if (spins > limit) {
                         atomicOr(err, kErrTimeout);
                         break;
                     }

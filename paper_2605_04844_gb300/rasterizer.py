@@ -66,7 +66,7 @@ def scene_struct(scene) -> N.QbScene:
     return s
 
 
-SORT_MODES = {"depth_first": 0, "full_key": 1, "chunked": 2}
+SORT_MODES = {"depth_first": 0, "full_key": 1}
 
 
 class Frame:
@@ -155,6 +155,7 @@ class Frame:
             "t_final": self._view(a.t_final, torch.float32, (H, W)),
             "n_contrib": self._view(a.n_contrib, torch.int32, (H, W)),
             "n_eval": self._view(a.n_eval, torch.int32, (H, W)),
+            "err_flags": self._view(a.err_flags, torch.int32, (2,)),
         }
 
 
