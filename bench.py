@@ -157,13 +157,16 @@ def run_ours(args, rank, world, local_rank):
     scene_s, cam_s = R.scene_struct(sd), R.camera_struct(cam)
     bg = (0.0, 0.0, 0.0)
 
-    # autotuned sort digit width unless given
+    # autotuned sort digit width and render batch depth unless the digit
+    # width is given
     digit_bits = args.digit_bits
+    render_batch = 128
     tune = None
     if digit_bits is None:
         from paper_2605_04844_gb300 import autotune
         tune = autotune.tune_frame(sd, cam, mode="quadbox")
         digit_bits = tune["digit_bits"]
+        render_batch = tune.get("render_batch", render_batch)
 
     frames, pairs = {}, {}
     for mode in ("quadbox", "aabb3s"):
@@ -171,12 +174,12 @@ def run_ours(args, rank, world, local_rank):
         pairs[mode] = fr.n_pairs
         cap = int(fr.n_pairs * 1.1) + 4096
         frames[mode] = R.Frame(n, W, H, cap)
-        frames[mode].set_tuning(digit_bits=digit_bits, sort_mode=args.sort_mode)
+        frames[mode].set_tuning(digit_bits=digit_bits, sort_mode=args.sort_mode, render_batch=render_batch)
     # the same QuadBox frame with the other pair-ordering schemes, for comparison
     other_modes = [m for m in ("depth_first", "full_key") if m != args.sort_mode]
     for m in other_modes:
         frames["quadbox_" + m] = R.Frame(n, W, H, int(pairs["quadbox"] * 1.1) + 4096)
-        frames["quadbox_" + m].set_tuning(digit_bits=8, sort_mode=m)
+        frames["quadbox_" + m].set_tuning(digit_bits=8, sort_mode=m, render_batch=render_batch)
     img = torch.empty((3, H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     grads = {k: torch.zeros_like(sd[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
@@ -308,8 +311,12 @@ def run_ours(args, rank, world, local_rank):
     fr.sort()
     fr.render(bg, img)
     torch.cuda.synchronize()
-    A = fr.arrays(n_pairs=1)
-    n_eval = int(A["n_eval"].to(torch.int64).sum().item()) if "n_eval" in A else None
+    # the method's render work: (pixel, entry) evaluations and those whose
+    # power test passed, counted by the counted variant of the same render
+    cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+    N.qb_render_fwd_counted(fr.frame, bg, img, cnt)
+    torch.cuda.synchronize()
+    n_eval, n_pass = (int(x) for x in cnt.cpu().tolist())
 
     # ---- end to end through the public API with host buffers ----
     host_img = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
@@ -354,7 +361,7 @@ def run_ours(args, rank, world, local_rank):
                                "same kernels",
                    "n_gaussians": n, "width": W, "height": H, "sh_degree": 3,
                    "l2": "flushed between timed steps (258 MB write); scene 236 MB > L2",
-                   "sort_digit_bits": digit_bits, "sort_mode": args.sort_mode,
+                   "sort_digit_bits": digit_bits, "render_batch": render_batch, "sort_mode": args.sort_mode,
                    "parallelism": f"replicas x{world}"},
         "quadbox": {"fwd_fps": round(1000.0 / fwd_ms, 2), "fwd_ms": round(fwd_ms, 4),
                     "fwd_bwd_ms": round(fb_ms, 4), "pairs_per_frame": P,
@@ -373,8 +380,10 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": round(wall, 2),
     }
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    result["roofline"] = roofline(fwd_stages, fwd_kernels, P, n, W, H, digit_bits, n_eval, clk, args.sort_mode,
-                                  sms=sms)
+    result["roofline"] = roofline(fwd_stages, fwd_kernels, P, n, W, H, digit_bits, (n_eval, n_pass), clk,
+                                  args.sort_mode, sms=sms)
+    result["render_work"] = {"evaluations": n_eval, "power_test_passed": n_pass,
+                             "flops": RENDER_FLOPS_POWER_TEST * n_eval + RENDER_FLOPS_PASSED * n_pass}
     result["roofline_kernels"] = result["roofline"].pop("kernels", {})
     result["kernels_fwd"] = fwd_kernels
     # counted by the library at each launch, inside the timed steps of every
@@ -385,9 +394,11 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
-def kernel_work(P, n, n_eval):
+def kernel_work(P, n, evals):
     """Algorithmic work per launch of each forward kernel at this frame: HBM
-    bytes (what the kernel must move at least) or FP32 operations."""
+    bytes (what the kernel must move at least) or FP32 operations.  evals:
+    (pixel-entry evaluations, those whose power test passed) of the render."""
+    n_eval, n_pass = evals if evals else (0, 0)
     return {
         "preprocess_kernel": ("hbm", n * PREPROCESS_BYTES),
         "sort_hist_kernel": ("hbm", n * 4),              # the depth keys once
@@ -397,7 +408,7 @@ def kernel_work(P, n, n_eval):
         "tile_count_kernel": ("hbm", P * 4),             # the tile ids once
         "tile_sort_pass": ("hbm", P * 16),               # key + value read and written
         "tile_sort_pass_values": ("hbm", P * 12),        # key + value read, value written
-        "render_kernel": ("alu", n_eval * RENDER_FLOPS_PER_EVAL if n_eval else 0),
+        "render_kernel": ("alu", n_eval * RENDER_FLOPS_POWER_TEST + n_pass * RENDER_FLOPS_PASSED),
     }
 
 
@@ -415,7 +426,7 @@ TRAFFIC_PER_UNIT = {
 }
 
 
-def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode, sms=152):
+def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, evals, clk, sort_mode, sms=152):
     """Roofline of the dominant kernel of the forward step: its algorithmic
     work per launch over its average launch duration, both measured in the
     timed steps (CUDA events recorded at each launch on the launching
@@ -428,7 +439,8 @@ def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, n_eval, clk, sort_mode
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    work = kernel_work(P, n, n_eval)
+    work = kernel_work(P, n, evals)
+    n_eval = evals[0] if evals else 0
     rows = {}
     for name, k in kernels.items():
         if name not in work or not k.get("ms_per_launch"):
@@ -736,8 +748,8 @@ def run_batch(args, dev):
         fr.check()
     K = len(cams)
     return {"workload": f"{args.batch_n} Gaussians, {K} cameras on a radius-8 sphere, resolutions from "
-                        "800x800/1264x832/1600x900/1920x1080, groups of 16 cameras",
-            "pairs_per_group": pairs, "tune": t,
+                        "800x800/1264x832/1600x900/1920x1080, preprocess in groups of 16, one global render queue",
+            "pairs_total": int(sum(pairs)), "pairs_max_camera": int(max(pairs)), "tune": t,
             "graph_fwd_ms": round(g_fwd, 3), "graph_fwd_bwd_ms": round(g_fb, 3),
             "separate_fwd_ms": round(sep_fwd, 3), "separate_fwd_bwd_ms": round(sep_fb, 3),
             "graph_fwd_cams_per_s": round(K * 1000.0 / g_fwd, 1),
@@ -756,11 +768,14 @@ KERNEL_TIMING_SPIN_CYCLES = 8_000_000
 # out, which understates the kernel's fraction slightly.
 PREPROCESS_BYTES = 236 + 76
 
-# FP32 operations per evaluated (pixel, Gaussian) entry of render_kernel:
-# dx, dy (2), power (3 mul + 2 fma + 1 neg-mul = 6), compare (1), exp (2:
-# scale + ex2), o*G (1), min (1), compare (1), 1-alpha (1), T*(1-alpha) (1),
-# compare (1), alpha*T (1), 3 colour FMAs (3).
-RENDER_FLOPS_PER_EVAL = 22
+# FP32 arithmetic of Eq. 2's per-pixel loop (an FMA counts 2, comparisons
+# and min/max none).  Every evaluated (pixel, entry): d = mu - p (2 sub), the
+# power a' dx^2 + b' dx dy + c' dy^2 as dx (a' dx) + dy (c' dy + b' dx)
+# (3 mul + 2 FMA) = 9.  An entry whose power test passes also takes alpha =
+# o exp(power) (exp 1 + its argument scaling 1 + mul 1), T' = T (1 - alpha)
+# (sub 1 + mul 1), the weight alpha T (mul 1) and three colour FMAs (6) = 12.
+RENDER_FLOPS_POWER_TEST = 9
+RENDER_FLOPS_PASSED = 12
 
 
 # --------------------------------------------------------------------------

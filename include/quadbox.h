@@ -272,6 +272,16 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream);
  * frame's t_final and n_contrib, which qb_render_bwd needs. */
 qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_stream_t stream);
 
+/* Measurement only: qb_render_fwd (identical outputs) that also adds, over
+ * all pixels, the (pixel, entry) evaluations of Eq. 2's loop up to each
+ * pixel's stop to d_counts[0] and those whose exponent passed the power test
+ * (power <= 0 and not below the skip threshold, i.e. alpha was computed) to
+ * d_counts[1].  d_counts: device uint64[2], accumulated (zero them first),
+ * 8-byte aligned.  The counted kernel is slower than qb_render_fwd's; the
+ * counts give the method's arithmetic work per frame for a roofline. */
+qb_status qb_render_fwd_counted(qb_frame *frame, const float *bg, float *d_img, uint64_t *d_counts,
+                                qb_stream_t stream);
+
 /* Backward of stages 1 and 4 (differentiable rasteriser, Sec. 4.1): walks each
  * tile list in reverse from every pixel's last contributor, recomputing the
  * transmittance by division, and accumulates into grads the gradient of
@@ -327,7 +337,7 @@ qb_status qb_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, uint64_t *d_keys_alt
  *  tiles_per_fetch  tiles a persistent render block takes from the global
  *                   tile-work queue at a time (1..8)
  *  render_batch     Gaussians staged per shared-memory batch (64, 128, 256)
- *  sort_digit_bits  radix digit width of the tile sort (8..11)
+ *  sort_digit_bits  radix digit width of each camera's tile sort (8..11)
  *  blocks_per_sm    persistent render blocks per SM (0: as many as fit) */
 typedef struct {
     int32_t tiles_per_fetch;
@@ -336,13 +346,17 @@ typedef struct {
     int32_t blocks_per_sm;
 } qb_tune;
 
-/* Batch state.  Cameras are processed in groups of `group` (<= QB_GROUP_MAX);
- * within a group all stages run as one kernel each over every camera, and
- * the render is one persistent kernel fed by a global queue over all the
- * group's tiles, so cameras of uneven resolution balance.  Images are packed
- * in one float buffer: camera k's planar [3][height][width] image starts at
- * float offset image_offset[k].  pair_capacity bounds the Gaussian-tile pairs
- * of one group (<= 2^30).  Fields are read-only for the caller. */
+/* Batch state.  The preprocess runs once per group of `group` cameras
+ * (<= QB_GROUP_MAX; one launch over every (camera, Gaussian) record of the
+ * group, reading the scene once); every camera's pairs are then binned and
+ * sorted like a frame into the camera's own slot; the render is one
+ * persistent kernel fed by a global queue over the tiles of all n_cams
+ * cameras, so cameras of uneven resolution balance across the GPU.  Images
+ * are packed in one float buffer: camera k's planar [3][height][width] image
+ * starts at float offset image_offset[k].  pair_capacity bounds the
+ * Gaussian-tile pairs of one camera (<= 2^30).  A camera may have at most
+ * 24576 tiles (render larger images as frames), and n_cams * n < 2^32.
+ * Fields are read-only for the caller. */
 typedef struct {
     int32_t n, n_cams, group, n_groups;
     uint64_t pair_capacity;
@@ -359,16 +373,19 @@ typedef struct {
 size_t qb_batch_workspace_bytes(int32_t n, int32_t n_cams, const int32_t *widths, const int32_t *heights,
                                 int32_t group, uint64_t pair_capacity);
 
-/* Binds a caller-owned, 256-byte aligned device workspace to *batch. */
+/* Binds a caller-owned, 256-byte aligned device workspace to *batch and
+ * writes the render's per-camera table into it (synchronises the stream
+ * once).  Errors: INVALID_ARG for sizes outside the limits above. */
 qb_status qb_batch_init(qb_batch *batch, int32_t n, int32_t n_cams, const int32_t *widths, const int32_t *heights,
                         int32_t group, uint64_t pair_capacity, void *d_workspace, size_t workspace_bytes,
                         qb_stream_t stream);
 
-/* Forward of every camera of the batch:
- * per group, one preprocess over all (camera, Gaussian) records, depth
- * order, scan, QPass emit with tile ids global over the group, a stable sort
- * on those ids, the ranges from the sorted ids, and one persistent render
- * over the group's tiles.  cams: host array of
+/* Forward of every camera of the batch (Sec. 2's pipeline with QuadBox
+ * binning, Sec. 3, per camera): per group, one preprocess over all (camera,
+ * Gaussian) records; per camera, the depth order of its records, scan, QPass
+ * emit with camera-local tile ids, the tile histogram (ranges and bucket
+ * offsets) and the stable tile sort into the camera's slot; then one
+ * persistent render over the tiles of every camera.  cams: host array of
  * n_cams cameras whose sizes match qb_batch_init; tune: host, NULL for
  * defaults; d_images: device floats, total_floats of them.  No host
  * synchronisation and no allocation, so a call can be captured in a CUDA
@@ -379,14 +396,16 @@ qb_status qb_render_batch(qb_batch *batch, const qb_scene *scene, const qb_camer
                           const qb_tune *tune, const float *bg, float *d_images, qb_stream_t stream);
 
 /* Backward of the last qb_render_batch (same scene, cameras and bg):
- * accumulates into grads the gradient of sum(d_dL_dimages * images).
- * d_dL_dimages is packed like the images.  Capturable like the forward. */
+ * accumulates into grads the gradient of sum(d_dL_dimages * images): one
+ * persistent render backward over every camera's tiles, then the chain to
+ * the scene parameters once per group.  d_dL_dimages is packed like the
+ * images.  Capturable like the forward. */
 qb_status qb_render_batch_bwd(qb_batch *batch, const qb_scene *scene, const qb_camera *cams, const float *bg,
                               const float *d_dL_dimages, qb_scene_grads *grads, qb_stream_t stream);
 
 /* Synchronises and reports overflow or time-outs of the last batch calls;
- * if pairs_out (host, n_groups entries) is non-NULL it receives the pairs
- * of every group. */
+ * if pairs_out (host, n_cams entries) is non-NULL it receives the pairs of
+ * every camera. */
 qb_status qb_batch_check(qb_batch *batch, uint64_t *pairs_out, qb_stream_t stream);
 
 /* The same sort for callers that may not allocate device memory (no

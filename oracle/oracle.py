@@ -260,19 +260,25 @@ def render_backward(W, H, ranges, vals, proj, dL_dimg, bg=(0.0, 0.0, 0.0)):
     return g_xy, g_con, g_o, g_rgb
 
 
-def render_backward_pixels(W, H, pxs, pys, dL, ranges, vals, proj, bg=(0.0, 0.0, 0.0)):
+def render_backward_pixels(W, H, pxs, pys, dL, ranges, vals, proj, bg=(0.0, 0.0, 0.0), magnitudes=False):
     """render_backward restricted to the listed pixels (dL [m,3] their loss
-    gradients): equal to render_backward with dL_dimg zero elsewhere."""
+    gradients): equal to render_backward with dL_dimg zero elsewhere.  With
+    magnitudes, also returns the per-entry sums of the terms' absolute
+    values (same shapes), the scale of a float32 evaluation's rounding error."""
     pxs, pys = _i32(pxs), _i32(pys)
     ranges = np.ascontiguousarray(ranges, dtype=np.int64)
     vals = _i32(vals) if len(vals) else np.zeros(1, dtype=np.int32)
     proj = _f64(proj)
     n = int(proj.shape[0])
     g_xy = np.zeros((n, 2)); g_con = np.zeros((n, 3)); g_o = np.zeros(n); g_rgb = np.zeros((n, 3))
+    a = [np.zeros((n, 2)), np.zeros((n, 3)), np.zeros(n), np.zeros((n, 3))] if magnitudes else None
+    ap = [_p(x) for x in a] if magnitudes else [None] * 4
     lib().orc_render_backward_pixels(ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(int(pxs.shape[0])), _p(pxs),
                                      _p(pys), _p(ranges), _p(vals), _p(proj), _p(_f64(bg)),
                                      _p(_f64(np.asarray(dL).reshape(-1, 3))), _p(g_xy), _p(g_con), _p(g_o),
-                                     _p(g_rgb))
+                                     _p(g_rgb), *ap)
+    if magnitudes:
+        return (g_xy, g_con, g_o, g_rgb), tuple(a)
     return g_xy, g_con, g_o, g_rgb
 
 

@@ -520,8 +520,11 @@ void orc_emit(int n, const int32_t *rects, int use_qpass, int tiles_x, const int
 /* the 1/255 skip and the 1e-4 stop are 3DGS conventions.)                   */
 /*                                                                           */
 /* amb[p] flags pixels whose discrete decisions are within a float32        */
-/* rounding band of their thresholds (alpha vs 1/255, T' vs 1e-4, and two   */
-/* consecutive contributors of nearly equal depth).                          */
+/* evaluation's error of their thresholds: alpha vs 1/255 and o G vs the     */
+/* 0.99 cap within 1e-3 relative (a float32 alpha carries |power| times the */
+/* conic's relative error, up to ~1e-4 for ill-conditioned projections),    */
+/* T' vs 1e-4 within 1e-3, and two consecutive contributors of nearly equal */
+/* depth.                                                                    */
 /* ------------------------------------------------------------------------ */
 
 static void composite_pixel(int px, int py, const int32_t *ids, int64_t cnt, const double *proj,
@@ -537,9 +540,11 @@ static void composite_pixel(int px, int py, const int32_t *ids, int64_t cnt, con
         double q = p[F_A] * dx * dx + 2.0 * p[F_B] * dx * dy + p[F_C] * dy * dy;
         double power = -0.5 * q;
         if (power > 0.0) continue;
-        double alpha = fmin(0.99, p[F_O] * exp(power));
-        if (fabs(alpha / ALPHA_MIN - 1.0) < 1e-4) a = 1;
+        double oG = p[F_O] * exp(power);
+        double alpha = fmin(0.99, oG);
+        if (fabs(alpha / ALPHA_MIN - 1.0) < 1e-3) a = 1;
         if (alpha < ALPHA_MIN) continue;
+        if (fabs(oG / 0.99 - 1.0) < 1e-3) a = 1;
         double testT = T * (1.0 - alpha);
         if (fabs(testT / 1e-4 - 1.0) < 1e-3) a = 1;
         if (prev_depth >= 0.0 && fabs(p[F_DEPTH] - prev_depth) <= 1e-6 * p[F_DEPTH]) a = 1;
@@ -658,9 +663,13 @@ typedef struct {
     int *cap;
 } orc_bwd_scratch;
 
+/* With a_xy etc. non-NULL, every accumulated term's absolute value is
+ * summed there too (the magnitude sum_p |term_p| of each gradient entry,
+ * the scale of its rounding error when the terms are computed in float32). */
 static void backward_pixel(int px, int py, const int32_t *ids, int64_t cnt, const double *proj,
                            const double *bg, const double g[3], orc_bwd_scratch *w, double *g_xy,
-                           double *g_conic, double *g_o, double *g_rgb)
+                           double *g_conic, double *g_o, double *g_rgb, double *a_xy, double *a_conic,
+                           double *a_o, double *a_rgb)
 {
     double T = 1.0;
     int m = 0;
@@ -691,10 +700,12 @@ static void backward_pixel(int px, int py, const int32_t *ids, int64_t cnt, cons
             }
             behind[ch] = sacc;
         }
-        double dL_dalpha = 0.0;
+        double dL_dalpha = 0.0, dL_dalpha_abs = 0.0;
         for (int ch = 0; ch < 3; ++ch) {
             g_rgb[3 * (size_t)w->id[k] + ch] += w->T[k] * w->a[k] * g[ch];
             dL_dalpha += g[ch] * (w->T[k] * p[F_R + ch] - behind[ch] / (1.0 - w->a[k]));
+            dL_dalpha_abs += fabs(g[ch]) * (w->T[k] * p[F_R + ch] + behind[ch] / (1.0 - w->a[k]));
+            if (a_rgb) a_rgb[3 * (size_t)w->id[k] + ch] += fabs(w->T[k] * w->a[k] * g[ch]);
         }
         if (w->cap[k]) continue;
         double G = w->G[k], o = p[F_O];
@@ -706,6 +717,15 @@ static void backward_pixel(int px, int py, const int32_t *ids, int64_t cnt, cons
         g_conic[3 * (size_t)w->id[k] + 2] += dL_dq * dy * dy;
         g_xy[2 * (size_t)w->id[k] + 0] += dL_dq * 2.0 * (p[F_A] * dx + p[F_B] * dy);
         g_xy[2 * (size_t)w->id[k] + 1] += dL_dq * 2.0 * (p[F_B] * dx + p[F_C] * dy);
+        if (a_o) {
+            double q_abs = dL_dalpha_abs * o * G * 0.5;
+            a_o[w->id[k]] += G * dL_dalpha_abs;
+            a_conic[3 * (size_t)w->id[k] + 0] += q_abs * dx * dx;
+            a_conic[3 * (size_t)w->id[k] + 1] += q_abs * 2.0 * fabs(dx * dy);
+            a_conic[3 * (size_t)w->id[k] + 2] += q_abs * dy * dy;
+            a_xy[2 * (size_t)w->id[k] + 0] += q_abs * 2.0 * (fabs(p[F_A] * dx) + fabs(p[F_B] * dy));
+            a_xy[2 * (size_t)w->id[k] + 1] += q_abs * 2.0 * (fabs(p[F_B] * dx) + fabs(p[F_C] * dy));
+        }
     }
 }
 
@@ -751,18 +771,20 @@ void orc_render_backward(int W, int H, const int64_t *ranges, const int32_t *val
             size_t pix = (size_t)py * W + px;
             double g[3] = { dL_dimg[pix], dL_dimg[(size_t)W * H + pix], dL_dimg[2 * (size_t)W * H + pix] };
             backward_pixel(px, py, vals + ranges[2 * t], ranges[2 * t + 1] - ranges[2 * t], proj, bg, g, &w,
-                           g_xy, g_conic, g_o, g_rgb);
+                           g_xy, g_conic, g_o, g_rgb, NULL, NULL, NULL, NULL);
         }
     bwd_scratch_free(&w);
 }
 
 /* The same sums over the m listed pixels (pxs[k], pys[k]) only, with their
  * loss gradients dL[k][3]; equal to orc_render_backward with dL_dimg zero
- * at every other pixel. */
+ * at every other pixel.  a_xy, a_conic, a_o, a_rgb (all NULL, or all
+ * non-NULL and zeroed) receive the sums of the terms' absolute values. */
 void orc_render_backward_pixels(int W, int H, int m, const int32_t *pxs, const int32_t *pys,
                                 const int64_t *ranges, const int32_t *vals, const double *proj,
                                 const double *bg, const double *dL, double *g_xy, double *g_conic,
-                                double *g_o, double *g_rgb)
+                                double *g_o, double *g_rgb, double *a_xy, double *a_conic, double *a_o,
+                                double *a_rgb)
 {
     int tiles_x = (W + ORC_TILE - 1) / ORC_TILE;
     orc_bwd_scratch w;
@@ -771,7 +793,7 @@ void orc_render_backward_pixels(int W, int H, int m, const int32_t *pxs, const i
         int px = pxs[k], py = pys[k];
         int t = (py / ORC_TILE) * tiles_x + px / ORC_TILE;
         backward_pixel(px, py, vals + ranges[2 * t], ranges[2 * t + 1] - ranges[2 * t], proj, bg, dL + 3 * (size_t)k,
-                       &w, g_xy, g_conic, g_o, g_rgb);
+                       &w, g_xy, g_conic, g_o, g_rgb, a_xy, a_conic, a_o, a_rgb);
     }
     bwd_scratch_free(&w);
 }

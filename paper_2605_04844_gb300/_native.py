@@ -101,6 +101,7 @@ _SIGS = [
     ("qb_bin_emit", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(c_u64), c_vp]),
     ("qb_sort", c_i32, [ctypes.POINTER(QbFrame), c_vp]),
     ("qb_render_fwd", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(c_f), c_vp, c_vp]),
+    ("qb_render_fwd_counted", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(c_f), c_vp, c_vp, c_vp]),
     ("qb_render_bwd", c_i32, [ctypes.POINTER(QbFrame), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera),
                               ctypes.POINTER(c_f), c_vp, ctypes.POINTER(QbSceneGrads), c_vp, c_vp]),
     ("qb_l1_loss_grad", c_i32, [c_vp, c_vp, c_vp, c_u64, ctypes.c_float, c_vp, c_vp]),
@@ -239,6 +240,11 @@ def qb_render_fwd(frame: QbFrame, bg, img, stream=None):
     check(load().qb_render_fwd(ctypes.byref(frame), _bg(bg), ptr(img), stream_handle(stream)))
 
 
+def qb_render_fwd_counted(frame: QbFrame, bg, img, counts, stream=None):
+    """counts: device int64 tensor of 2 entries, accumulated (zero it first)."""
+    check(load().qb_render_fwd_counted(ctypes.byref(frame), _bg(bg), ptr(img), ptr(counts), stream_handle(stream)))
+
+
 def qb_render_bwd(frame: QbFrame, scene: QbScene, camera: QbCamera, bg, dL_dimg, grads: QbSceneGrads,
                   grad_screen=None, stream=None):
     check(load().qb_render_bwd(ctypes.byref(frame), ctypes.byref(scene), ctypes.byref(camera), _bg(bg),
@@ -310,7 +316,7 @@ def qb_render_batch_bwd(batch: QbBatch, scene: QbScene, cams_array, bg, dL_dimag
 
 
 def qb_batch_check(batch: QbBatch, stream=None):
-    """Returns the pairs of every group (synchronises)."""
-    out = (c_u64 * max(1, batch.n_groups))()
+    """Returns the pairs of every camera (synchronises)."""
+    out = (c_u64 * max(1, batch.n_cams))()
     check(load().qb_batch_check(ctypes.byref(batch), out, stream_handle(stream)))
-    return [int(out[i]) for i in range(batch.n_groups)]
+    return [int(out[i]) for i in range(batch.n_cams)]

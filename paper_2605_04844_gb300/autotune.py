@@ -1,8 +1,12 @@
 """Autotuner for the rasteriser's launch parameters.
 
 Times the candidates on the caller's own scene and camera and keeps the
-fastest: the sort's radix digit width (8..11 bits, which sets the number of
-onesweep passes).  Results are cached as JSON under
+fastest.  For a frame: the tile sort's radix digit width (8..11 bits, which
+sets the number of onesweep passes), then the render's per-tile batch depth
+(Gaussians staged in shared memory per step).  For a batch of cameras: the
+digit width, batch depth, tiles a persistent render block takes per fetch
+from the global queue and persistent blocks per SM, by coordinate descent.
+Results are cached as JSON under
 $QUADBOX_CACHE_DIR (default ~/.cache/quadbox/tune.json), keyed by GPU name,
 Gaussian count, image size and binning mode.
 """
@@ -16,6 +20,7 @@ import torch
 from . import rasterizer as R
 
 DIGIT_CANDIDATES = (8, 9, 10, 11)
+RENDER_BATCH_CANDIDATES = (64, 128, 256)
 
 
 def _cache_path():
@@ -52,10 +57,11 @@ def _time(fn, reps):
 
 
 def tune_frame(scene, cam, mode="quadbox", reps=5, use_cache=True):
-    """Pick the sort digit width for this scene and camera."""
+    """Pick the sort digit width (timing preprocess, emit and sort), then the
+    render's batch depth (timing the render), for this scene and camera."""
     n = int(scene["means"].shape[0])
     W, H = int(cam["width"]), int(cam["height"])
-    key = f"{torch.cuda.get_device_name()}|n={n}|{W}x{H}|{mode}"
+    key = f"{torch.cuda.get_device_name()}|frame2|n={n}|{W}x{H}|{mode}"
     db = _load() if use_cache else {}
     if key in db:
         return dict(db[key], cached=True)
@@ -72,7 +78,21 @@ def tune_frame(scene, cam, mode="quadbox", reps=5, use_cache=True):
         run()
         timings[d] = _time(run, reps)
     best = min(timings, key=timings.get)
-    res = {"digit_bits": int(best), "ms": {str(k): round(v, 4) for k, v in timings.items()}}
+    fr.set_tuning(digit_bits=best)
+    fr.preprocess(scene_s, cam_s, mode)
+    fr.bin_emit(sync=False)
+    fr.sort()
+    img = torch.empty((3, H, W), dtype=torch.float32, device=fr.ws.device)
+    rtimes = {}
+    for rb in RENDER_BATCH_CANDIDATES:
+        fr.set_tuning(render_batch=rb)
+        fr.render(None, img)
+        rtimes[rb] = _time(lambda: fr.render(None, img), reps)
+    fr.check()
+    best_rb = min(rtimes, key=rtimes.get)
+    res = {"digit_bits": int(best), "render_batch": int(best_rb),
+           "ms": {str(k): round(v, 4) for k, v in timings.items()},
+           "render_ms": {str(k): round(v, 4) for k, v in rtimes.items()}}
     if use_cache:
         db[key] = res
         _save(db)

@@ -50,6 +50,7 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     };
     const size_t N = (size_t)n;
     L.xy = take(8 * N);
+    L.shape = take(8 * N);
     L.conic_o = take(16 * N);
     L.rgbd = take(16 * N);
     L.box = take(16 * N);
@@ -319,6 +320,7 @@ qb_status qb_preprocess(qb_frame *frame, const qb_scene *scene, const qb_camera 
     a.mode = base_mode;
     a.clamp3s = (mode & QB_BIN_NO_CLAMP) == 0;
     a.xy = at<float2>(frame, L.xy);
+    a.shape = at<float2>(frame, L.shape);
     a.conic_o = at<float4>(frame, L.conic_o);
     a.rgbd = at<float4>(frame, L.rgbd);
     a.box = at<float4>(frame, L.box);
@@ -520,16 +522,19 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
     return QB_OK;
 }
 
-qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_stream_t stream) {
+static qb_status render_fwd_impl(qb_frame *frame, const float *bg, float *d_img, unsigned long long *counts,
+                                 qb_stream_t stream) {
     Layout L;
     qb_status st = check_frame(frame, L);
     if (st != QB_OK) return st;
     if (frame->stage < 3) return fail(QB_ERR_STATE, "qb_render_fwd before qb_sort");
     if (!d_img) return fail(QB_ERR_INVALID_ARG, "image pointer is NULL");
     RenderArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.ranges = at<uint2>(frame, L.ranges);
     a.vals = at<uint32_t>(frame, frame->sorted_in_alt ? L.vals1 : L.vals0);
     a.xy = at<float2>(frame, L.xy);
+    a.shape = at<float2>(frame, L.shape);
     a.conic_o = at<float4>(frame, L.conic_o);
     a.rgbd = at<float4>(frame, L.rgbd);
     a.ts = frame_tileset(frame);
@@ -541,9 +546,21 @@ qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_strea
     a.tfinal = at<float>(frame, L.tfinal);
     a.ncontrib = at<int>(frame, L.ncontrib);
     a.neval = at<int>(frame, L.neval);
+    a.counts = counts;
     QB_CUDA(launch_render(a, frame->render_batch, (cudaStream_t)stream));
     frame->stage = 4;
     return QB_OK;
+}
+
+qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_stream_t stream) {
+    return render_fwd_impl(frame, bg, d_img, nullptr, stream);
+}
+
+qb_status qb_render_fwd_counted(qb_frame *frame, const float *bg, float *d_img, uint64_t *d_counts,
+                                qb_stream_t stream) {
+    if (!d_counts) return fail(QB_ERR_INVALID_ARG, "counts pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(d_counts) % 8 != 0) return fail(QB_ERR_INVALID_ARG, "counts must be 8-byte aligned");
+    return render_fwd_impl(frame, bg, d_img, reinterpret_cast<unsigned long long *>(d_counts), stream);
 }
 
 qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, const float *bg,
@@ -565,9 +582,11 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
         QB_CUDA(cudaMemsetAsync(gscreen, 0, 72 * (size_t)frame->n, s));
     }
     BwdArgs b;
+    std::memset(&b, 0, sizeof(b));
     b.ranges = at<uint2>(frame, L.ranges);
     b.vals = at<uint32_t>(frame, frame->sorted_in_alt ? L.vals1 : L.vals0);
     b.xy = at<float2>(frame, L.xy);
+    b.shape = at<float2>(frame, L.shape);
     b.conic_o = at<float4>(frame, L.conic_o);
     b.rgbd = at<float4>(frame, L.rgbd);
     b.ts = frame_tileset(frame);

@@ -31,6 +31,7 @@ namespace qb {
 
 constexpr int kBwdPix = 4;                            // pixels per thread (one column)
 constexpr int kBwdThreads = kTile * kTile / kBwdPix;  // threads per tile
+static_assert(kBwdThreads == 64 && kBwdPix == 4, "two warps per tile, each a half tile of 16 x 8 pixels");
 constexpr int kBwdBatch = 128;  // entries staged per shared-memory batch
 
 // float -> double by rebuilding the IEEE-754 bit pattern with integer
@@ -86,11 +87,14 @@ __device__ __forceinline__ void warp_reduce9_add(const float g[9], double *dst, 
 // Staged entries of a backward batch, laid out for the packed FP32x2
 // arithmetic (operands the pixels of a thread share are stored twice):
 //   s0 = (mu_x, mu_x, mu_y, mu_y), s1 = (ca, ca, cb, cb),
-//   s2 = (cc, cc, skip threshold, -), s3 = (r, r, g, g), s4 = (b, b, o, o),
-// with (ca, cb, cc) = (-a/2, -b, -c/2) the rescaled conic of the forward.
+//   s2 = (cc, cc, skip threshold, elongated), s3 = (r, r, g, g), s4 = (b, b, o, o),
+//   s5 = (rr, rr, ce, ce),
+// with (ca, cb, cc) = (-a/2, -b, -c/2) the rescaled conic of the forward and,
+// for an elongated Gaussian (s2.w = 1), the exact power form's terms
+// (qb_render.cu): power = ca u^2 + ce dy^2, u = dx + rr dy.
 struct BwdStage {
     uint32_t *id;
-    float4 *s0, *s1, *s2, *s3, *s4;
+    float4 *s0, *s1, *s2, *s3, *s4, *s5;
     int *maxlast;
 };
 
@@ -106,9 +110,11 @@ struct BwdPair {
     int last0, last1;
 };
 
-// A tile by kBwdThreads threads, each owning kBwdPix pixels of one column
-// (rows r, r + 4, r + 8, r + 12) as two packed pairs (r, r + 4) and
-// (r + 8, r + 12).  Per entry, for every pixel:
+// A tile by kBwdThreads threads: two warps, each owning one half of the tile
+// (rows 0-7 or 8-15, a compact footprint, so a small ellipse reaches one
+// warp more often than both); a thread owns kBwdPix pixels of one column of
+// its half (rows r, r + 2, r + 4, r + 6) as two packed pairs (r, r + 2) and
+// (r + 4, r + 6).  Per entry, for every pixel:
 //   T <- T / (1 - alpha)                       (T in front of the entry)
 //   dL/dc_k     += alpha T dL/dC
 //   dL/dalpha    = T S1 - S2 / (1 - alpha),    S1 = sum_c dL/dC_c c_k,c
@@ -119,13 +125,13 @@ struct BwdPair {
 //   dL/dmu += dpower v, dL/dSigma += dpower (vx^2/2, vx vy, vy^2/2).
 // An entry a pixel does not composite takes alpha = 0 (T, S2 unchanged, no
 // contribution), so the pairs run in lock step without branches.
-__device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile, int ci, const BwdStage &S) {
-    const CamTile &C = a.ts.cam[ci];
+__device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile, const CamTile &C, const BwdStage &S) {
     const uint32_t lt = gtile - C.tile_base;
+    const uint32_t *vals = a.vals + C.vals_base;
     const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31;
-    const int px = tx * kTile + (tid & (kTile - 1));
-    const int py_first = ty * kTile + (tid >> kTileShift);
+    const int px = tx * kTile + (lane & (kTile - 1));
+    const int py_first = ty * kTile + (tid >> 5) * 8 + (lane >> kTileShift);
     const float2 npx = f2(-(float)px, -(float)px);
     const size_t plane = (size_t)C.W * C.H;
     const float *dl = a.dL_dimg + 3 * C.pix_base;
@@ -134,7 +140,7 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
     int mylast = 0;
 #pragma unroll
     for (int h = 0; h < kBwdPix; ++h) {
-        const int py = py_first + h * (kTile / kBwdPix);
+        const int py = py_first + 2 * h;
         float T = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
         int last = 0;
         if (px < C.W && py < C.H) {
@@ -168,17 +174,19 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
         const int start = end - cnt;
         __syncthreads();
         for (int k = tid; k < cnt; k += kBwdThreads) {
-            const uint32_t g = a.vals[rstart + start + k];
+            const uint32_t g = C.rec_base + vals[rstart + start + k];
             S.id[k] = g;
             const float2 m = a.xy[g];
             const float4 co = a.conic_o[g];
             const float4 rgb = a.rgbd[g];
+            const float2 sh = a.shape[g];
             const float ca = -0.5f * co.x, cb = -co.y, cc = -0.5f * co.z;
             S.s0[k] = make_float4(m.x, m.x, m.y, m.y);
             S.s1[k] = make_float4(ca, ca, cb, cb);
-            S.s2[k] = make_float4(cc, cc, skip_threshold(co.w), 0.f);
+            S.s2[k] = make_float4(cc, cc, skip_threshold(co.w), sh.y != 0.f ? 1.f : 0.f);
             S.s3[k] = make_float4(rgb.x, rgb.x, rgb.y, rgb.y);
             S.s4[k] = make_float4(rgb.z, rgb.z, co.w, co.w);
+            if (sh.y != 0.f) S.s5[k] = make_float4(sh.x, sh.x, sh.y, sh.y);  // read for elongated entries only
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
@@ -189,12 +197,29 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
             const float2 A = __fmul2_rn(cadx, dx);
             const float2 B = __fmul2_rn(f2(Q.z, Q.w), dx);
             const float2 cc2 = f2(K.x, K.y);
-            float2 dy[2], pw[2];
+            const bool elong = K.w != 0.f;  // the same for the whole warp
+            float2 dy[2], pw[2], cau[2];
+            float4 E;
+            if (!elong) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    dy[r] = __fadd2_rn(f2(X.z, X.w), P[r].npy);
+                    pw[r] = __ffma2_rn(dy[r], __ffma2_rn(cc2, dy[r], B), A);
+                }
+            } else {
+                // the forward's exact power form (the same operations)
+                E = S.s5[j];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    dy[r] = __fadd2_rn(f2(X.z, X.w), P[r].npy);
+                    const float2 u = __ffma2_rn(f2(E.x, E.y), dy[r], dx);
+                    cau[r] = __fmul2_rn(f2(Q.x, Q.y), u);
+                    pw[r] = __ffma2_rn(cau[r], u, __fmul2_rn(__fmul2_rn(f2(E.z, E.w), dy[r]), dy[r]));
+                }
+            }
             bool e[4];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                dy[r] = __fadd2_rn(f2(X.z, X.w), P[r].npy);
-                pw[r] = __ffma2_rn(dy[r], __ffma2_rn(cc2, dy[r], B), A);
                 e[2 * r] = p < P[r].last0 && pw[r].x <= 0.f && pw[r].x >= K.z;
                 e[2 * r + 1] = p < P[r].last1 && pw[r].y <= 0.f && pw[r].y >= K.z;
             }
@@ -223,8 +248,16 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
                 // derivative through o G where the cap does not bind
                 const float2 Gm = f2(c0 && oG.x < kAlphaMax ? G.x : 0.f, c1 && oG.y < kAlphaMax ? G.y : 0.f);
                 const float2 dp = __fmul2_rn(dal, __fmul2_rn(o2, Gm));
-                const float2 vx = __ffma2_rn(f2(Q.z, Q.w), dy[r], __fmul2_rn(two, cadx));
-                const float2 vy = __ffma2_rn(two, __fmul2_rn(cc2, dy[r]), B);
+                // dpower/dmu: (2 ca dx + cb dy, cb dx + 2 cc dy), or in the
+                // exact form (2 ca u, 2 ca u rr + 2 ce dy), which does not cancel
+                float2 vx, vy;
+                if (!elong) {
+                    vx = __ffma2_rn(f2(Q.z, Q.w), dy[r], __fmul2_rn(two, cadx));
+                    vy = __ffma2_rn(two, __fmul2_rn(cc2, dy[r]), B);
+                } else {
+                    vx = __fmul2_rn(two, cau[r]);
+                    vy = __ffma2_rn(__fmul2_rn(two, cau[r]), f2(E.x, E.y), __fmul2_rn(two, __fmul2_rn(f2(E.z, E.w), dy[r])));
+                }
                 const float2 dpvx = __fmul2_rn(dp, vx), dpvy = __fmul2_rn(dp, vy);
                 if (r == 0) {
                     X0 = dpvx;
@@ -260,18 +293,18 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
 
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
     __shared__ uint32_t s_id[kBwdBatch];
-    __shared__ float4 s_st[5][kBwdBatch];
+    __shared__ float4 s_st[6][kBwdBatch];
     __shared__ int s_maxlast;
-    const BwdStage S{s_id, s_st[0], s_st[1], s_st[2], s_st[3], s_st[4], &s_maxlast};
-    render_bwd_tile(a, blockIdx.x, 0, S);
+    const BwdStage S{s_id, s_st[0], s_st[1], s_st[2], s_st[3], s_st[4], s_st[5], &s_maxlast};
+    render_bwd_tile(a, blockIdx.x, a.ts.cam[0], S);
 }
 
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent_kernel(BwdArgs a) {
     __shared__ uint32_t s_id[kBwdBatch];
-    __shared__ float4 s_st[5][kBwdBatch];
+    __shared__ float4 s_st[6][kBwdBatch];
     __shared__ int s_maxlast;
     __shared__ uint32_t s_next;
-    const BwdStage S{s_id, s_st[0], s_st[1], s_st[2], s_st[3], s_st[4], &s_maxlast};
+    const BwdStage S{s_id, s_st[0], s_st[1], s_st[2], s_st[3], s_st[4], s_st[5], &s_maxlast};
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(a.queue, (uint32_t)a.tiles_per_fetch);
         __syncthreads();
@@ -279,7 +312,14 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent_kernel(BwdA
         __syncthreads();
         if (t0 >= a.ts.total_tiles) break;
         const uint32_t t1 = min(t0 + (uint32_t)a.tiles_per_fetch, a.ts.total_tiles);
-        for (uint32_t t = t0; t < t1; ++t) render_bwd_tile(a, t, camera_of(a.ts, t), S);
+        for (uint32_t t = t0; t < t1; ++t) {
+            if (a.cam_table) {
+                const CamTile C = a.cam_table[camera_in_table(a.cam_table, a.ts.n_cams, t)];
+                render_bwd_tile(a, t, C, S);
+            } else {
+                render_bwd_tile(a, t, a.ts.cam[camera_of(a.ts, t)], S);
+            }
+        }
     }
 }
 

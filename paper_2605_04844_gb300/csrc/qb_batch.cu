@@ -1,18 +1,24 @@
 // qb_batch.cu -- many cameras of one scene rendered together (include/quadbox.h,
-// qb_render_batch).  The cameras are taken in groups; for a group every stage
-// of the rasteriser runs once over all of its (camera, Gaussian) records:
-// preprocess (one grid row per camera), depth order of the records, scan,
-// QPass emit with tile ids global over the group, a stable sort on those ids
-// (per-pass digit histograms, every pass writing keys), the ranges from the
-// sorted ids, and a persistent render that takes tiles of any of the group's
-// cameras from one work queue.  (The group's ~10^5 tiles are too many for the
-// shared-memory tile histogram of the single-frame path, and counting them
-// from the preprocess by atomics on difference arrays cost more than the
-// sort's own histograms and a ranges pass.)  Nothing synchronises the host, so a whole call can be
-// captured in a CUDA graph.  The records, the sorted values, the ranges and
-// the per-pixel state of every camera stay in the workspace for
-// qb_render_batch_bwd.
+// qb_render_batch).  The cameras are taken in groups for the preprocess: one
+// launch projects the scene into every camera of a group (one grid row per
+// camera), so the scene's parameters and SH coefficients are read once per
+// group.  Each camera's pairs are then binned like a single frame -- depth
+// order of its records, scan, QPass emit with camera-local tile ids, the
+// shared-memory tile histogram (ranges and bucket offsets) and the two-pass
+// tile sort -- into the camera's own slot of sorted values.  Last, one
+// persistent render takes tiles of every camera of the batch from one global
+// work queue, so cameras of uneven resolution balance across the whole GPU
+// and no camera's tail leaves SMs idle before the next one starts.
+//
+// The per-camera geometry the render needs (tile and pixel bases, the slot of
+// sorted values, the first record) is fixed when the batch is initialised and
+// lives in a device table in the workspace.  Nothing synchronises the host,
+// so a whole call can be captured in a CUDA graph.  The records, the sorted
+// values, the ranges and the per-pixel state of every camera stay in the
+// workspace for qb_render_batch_bwd, whose render backward is one persistent
+// launch over all cameras' tiles as well.
 #include <cstring>
+#include <vector>
 
 #include "qb_kernels.cuh"
 
@@ -35,21 +41,8 @@ struct Geo {  // per-camera geometry of a batch
     int tx[QB_MAX_CAMERAS], ty[QB_MAX_CAMERAS];
     uint64_t tile_base[QB_MAX_CAMERAS + 1];
     uint64_t pix_base[QB_MAX_CAMERAS + 1];
+    int max_tile_bits, max_tiles;
 };
-
-bool make_geo(int n_cams, const int32_t *W, const int32_t *H, Geo &g) {
-    if (n_cams < 1 || n_cams > QB_MAX_CAMERAS || !W || !H) return false;
-    g.tile_base[0] = 0;
-    g.pix_base[0] = 0;
-    for (int k = 0; k < n_cams; ++k) {
-        if (W[k] <= 0 || H[k] <= 0 || W[k] > (1 << 15) || H[k] > (1 << 15)) return false;
-        g.tx[k] = (W[k] + kTile - 1) / kTile;
-        g.ty[k] = (H[k] + kTile - 1) / kTile;
-        g.tile_base[k + 1] = g.tile_base[k] + (uint64_t)g.tx[k] * g.ty[k];
-        g.pix_base[k + 1] = g.pix_base[k] + (uint64_t)W[k] * H[k];
-    }
-    return true;
-}
 
 int bits_for(uint64_t v) {  // bits to hold values < v
     int b = 0;
@@ -57,28 +50,45 @@ int bits_for(uint64_t v) {  // bits to hold values < v
     return b;
 }
 
+bool make_geo(int n_cams, const int32_t *W, const int32_t *H, Geo &g) {
+    if (n_cams < 1 || n_cams > QB_MAX_CAMERAS || !W || !H) return false;
+    g.tile_base[0] = 0;
+    g.pix_base[0] = 0;
+    g.max_tile_bits = 1;
+    g.max_tiles = 1;
+    for (int k = 0; k < n_cams; ++k) {
+        if (W[k] <= 0 || H[k] <= 0 || W[k] > (1 << 15) || H[k] > (1 << 15)) return false;
+        g.tx[k] = (W[k] + kTile - 1) / kTile;
+        g.ty[k] = (H[k] + kTile - 1) / kTile;
+        const int tiles = g.tx[k] * g.ty[k];
+        if (tiles > kTileCountMax) return false;  // beyond the tile histogram's shared memory
+        g.tile_base[k + 1] = g.tile_base[k] + (uint64_t)tiles;
+        g.pix_base[k + 1] = g.pix_base[k] + (uint64_t)W[k] * H[k];
+        g.max_tiles = tiles > g.max_tiles ? tiles : g.max_tiles;
+        const int tb = bits_for((uint64_t)tiles);
+        g.max_tile_bits = tb > g.max_tile_bits ? tb : g.max_tile_bits;
+    }
+    return g.tile_base[n_cams] < (1ull << 32);
+}
+
 struct BLayout {
-    size_t xy, conic_o, rgbd, box, r3, meta, counts;  // [n_cams * n]
-    size_t slots;                                     // [n_groups][cap] sorted values
+    size_t xy, shape, conic_o, rgbd, box, r3, meta, counts;  // [n_cams * n] records
+    size_t cam_table;                                 // [n_cams] CamTile
+    size_t slots;                                     // [n_cams][cap] sorted values per camera
     size_t ranges;                                    // [total tiles]
     size_t tfinal, ncontrib, neval;                   // [total pixels]
-    size_t keysA, keysB, valsT;                       // [cap] group scratch
-    size_t offsets, segs, scan_part, dk0, dk1, dv0, dv1;  // [group * n]
-    size_t dsort, sort, gscreen, queue, state;
+    size_t segs, dk0, dk1, dv0, dv1;                  // [group * n] group scratch
+    size_t keysA, keysB, valsT;                       // [cap] one camera's pair scratch
+    size_t offsets, scan_part, dsort, sort, tile_counts;
+    size_t gscreen;                                   // [n_cams * n][9]
+    size_t queue, state;
     size_t total;
 };
 
 bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLayout &L) {
     if (n < 0 || group < 1 || group > QB_GROUP_MAX || cap > (1ull << 30)) return false;
-    const int n_groups = (n_cams + group - 1) / group;
     const size_t recs = (size_t)n_cams * n, grecs = (size_t)group * n;
-    int max_tile_bits = 1;
-    for (int g0 = 0; g0 < n_cams; g0 += group) {
-        const int g1 = g0 + group < n_cams ? g0 + group : n_cams;
-        const int tb = bits_for(g.tile_base[g1] - g.tile_base[g0]);
-        max_tile_bits = tb > max_tile_bits ? tb : max_tile_bits;
-    }
-    if ((size_t)group * n > (size_t)INT32_MAX) return false;
+    if (grecs > (size_t)INT32_MAX || recs >= (1ull << 32)) return false;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -86,38 +96,42 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
         return o;
     };
     L.xy = take(8 * recs);
+    L.shape = take(8 * recs);
     L.conic_o = take(16 * recs);
     L.rgbd = take(16 * recs);
     L.box = take(16 * recs);
     L.r3 = take(4 * recs);
     L.meta = take(4 * recs);
     L.counts = take(4 * recs);
-    L.slots = take(4 * (size_t)n_groups * cap);
+    L.cam_table = take(sizeof(CamTile) * (size_t)n_cams);
+    L.slots = take(4 * (size_t)n_cams * cap);
     L.ranges = take(8 * g.tile_base[n_cams]);
     L.tfinal = take(4 * g.pix_base[n_cams]);
     L.ncontrib = take(4 * g.pix_base[n_cams]);
     L.neval = take(4 * g.pix_base[n_cams]);
-    L.keysA = take(4 * cap);
-    L.keysB = take(4 * cap);
-    L.valsT = take(4 * cap);
-    L.offsets = take(4 * grecs);
     L.segs = take(64 * grecs);
-    L.scan_part = take(8 * scan_partials_count((int)grecs));
     L.dk0 = take(4 * grecs);
     L.dk1 = take(4 * grecs);
     L.dv0 = take(4 * grecs);
     L.dv1 = take(4 * grecs);
+    L.keysA = take(4 * cap);
+    L.keysB = take(4 * cap);
+    L.valsT = take(4 * cap);
+    L.offsets = take(4 * (size_t)n);
+    L.scan_part = take(8 * scan_partials_count(n));
     size_t db = 0, sb = 0;
     for (int d = 8; d <= kMaxDigitBits; ++d) {
-        size_t b1 = sort_scratch_bytes(grecs, kDepthBits, d), b2 = sort_scratch_bytes(cap, max_tile_bits, d);
+        const size_t b1 = sort_scratch_bytes((uint64_t)n, kDepthBits, d);
+        const size_t b2 = sort_scratch_bytes(cap, g.max_tile_bits, d);
         db = b1 > db ? b1 : db;
         sb = b2 > sb ? b2 : sb;
     }
     L.dsort = take(db);
     L.sort = take(sb);
-    L.gscreen = take(72 * grecs);
+    L.tile_counts = take(4 * ((size_t)g.max_tiles + 1));
+    L.gscreen = take(72 * recs);
     L.queue = take(256);
-    L.state = take(8 * (size_t)n_groups + 256);
+    L.state = take(8 * (size_t)n_cams + 256);
     L.total = off;
     return true;
 }
@@ -125,6 +139,10 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
 template <typename T>
 T *bat(const qb_batch *b, size_t off) {
     return reinterpret_cast<T *>(static_cast<uint8_t *>(b->workspace) + off);
+}
+
+uint32_t *err_word(const qb_batch *b, const BLayout &L) {
+    return reinterpret_cast<uint32_t *>(bat<uint8_t>(b, L.state) + 8 * (size_t)b->n_cams);
 }
 
 CamDev cam_dev(const qb_camera &c) {
@@ -145,14 +163,28 @@ CamDev cam_dev(const qb_camera &c) {
     return d;
 }
 
-// Per-group views: camera set, tile set (tile ids local to the group, pixel
-// bases global), count-array offsets.
+// Camera k's entry of the render's table: global tile and pixel bases, its
+// slot of sorted values, and the first record of its group (the emitted
+// values are record indices within the group).
+CamTile cam_tile(const qb_batch *b, const Geo &g, int k) {
+    CamTile t;
+    std::memset(&t, 0, sizeof(t));
+    t.W = b->widths[k];
+    t.H = b->heights[k];
+    t.tiles_x = g.tx[k];
+    t.tiles_y = g.ty[k];
+    t.tile_base = (uint32_t)g.tile_base[k];
+    t.rec_base = (uint32_t)((size_t)(k - k % b->group) * b->n);
+    t.pix_base = g.pix_base[k];
+    t.vals_base = (uint64_t)k * b->pair_capacity;
+    return t;
+}
+
+// A group of cameras: camera set for the preprocess, and a tile set whose
+// cameras all start at tile 0 (each camera is binned on its own tiles).
 struct GroupView {
     int k0, k1, ncam;
-    uint64_t rec0;      // first record
-    uint64_t tile0;     // first global tile
-    uint32_t ntiles;
-    int tile_bits;
+    uint64_t rec0;  // first record
     CamSet cs;
     TileSet ts;
 };
@@ -163,12 +195,8 @@ void group_view(const qb_batch *b, const Geo &g, const qb_camera *cams, int gi, 
     v.k1 = v.k0 + b->group < b->n_cams ? v.k0 + b->group : b->n_cams;
     v.ncam = v.k1 - v.k0;
     v.rec0 = (uint64_t)v.k0 * b->n;
-    v.tile0 = g.tile_base[v.k0];
-    v.ntiles = (uint32_t)(g.tile_base[v.k1] - g.tile_base[v.k0]);
-    v.tile_bits = bits_for(v.ntiles);
     v.cs.n_cams = v.ncam;
     v.ts.n_cams = v.ncam;
-    v.ts.total_tiles = v.ntiles;
     for (int c = 0; c < v.ncam; ++c) {
         const int k = v.k0 + c;
         if (cams) v.cs.cam[c] = cam_dev(cams[k]);
@@ -176,9 +204,21 @@ void group_view(const qb_batch *b, const Geo &g, const qb_camera *cams, int gi, 
         v.ts.cam[c].H = b->heights[k];
         v.ts.cam[c].tiles_x = g.tx[k];
         v.ts.cam[c].tiles_y = g.ty[k];
-        v.ts.cam[c].tile_base = (uint32_t)(g.tile_base[k] - v.tile0);
+        v.ts.cam[c].tile_base = 0;
         v.ts.cam[c].pix_base = g.pix_base[k];
+        v.ts.total_tiles = v.ts.total_tiles > (uint32_t)(g.tx[k] * g.ty[k]) ? v.ts.total_tiles
+                                                                           : (uint32_t)(g.tx[k] * g.ty[k]);
     }
+}
+
+// The whole batch as one tile set for the persistent render and backward
+// (the cameras themselves come from the device table).
+TileSet batch_tileset(const qb_batch *b, const Geo &g) {
+    TileSet ts;
+    std::memset(&ts, 0, sizeof(ts));
+    ts.n_cams = b->n_cams;
+    ts.total_tiles = (uint32_t)g.tile_base[b->n_cams];
+    return ts;
 }
 
 qb_status check_batch(const qb_batch *b, Geo &g, BLayout &L) {
@@ -229,8 +269,10 @@ qb_status qb_batch_init(qb_batch *batch, int32_t n, int32_t n_cams, const int32_
     if (!batch) return bfail(QB_ERR_INVALID_ARG, "batch is NULL");
     Geo g;
     BLayout L;
-    if (!make_geo(n_cams, widths, heights, g) || !make_blayout(n, n_cams, group, pair_capacity, g, L))
-        return bfail(QB_ERR_INVALID_ARG, "invalid batch sizes");
+    if (!make_geo(n_cams, widths, heights, g))
+        return bfail(QB_ERR_INVALID_ARG, "invalid camera sizes (1..256 cameras of 1..32768 pixels a side, at most "
+                                         "24576 tiles each)");
+    if (!make_blayout(n, n_cams, group, pair_capacity, g, L)) return bfail(QB_ERR_INVALID_ARG, "invalid batch sizes");
     if (!d_workspace || reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
         return bfail(QB_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
     if (workspace_bytes < L.total) return bfail(QB_ERR_INVALID_ARG, "workspace too small");
@@ -248,8 +290,14 @@ qb_status qb_batch_init(qb_batch *batch, int32_t n, int32_t n_cams, const int32_
         batch->image_offset[k] = 3 * g.pix_base[k];
     }
     batch->total_floats = 3 * g.pix_base[n_cams];
-    QB_BCUDA(cudaMemsetAsync(bat<uint8_t>(batch, L.state), 0, 8 * (size_t)batch->n_groups + 256,
-                             (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    QB_BCUDA(cudaMemsetAsync(bat<uint8_t>(batch, L.state), 0, 8 * (size_t)n_cams + 256, s));
+    // the render's camera table: fixed by the cameras' sizes and the capacity
+    std::vector<CamTile> table((size_t)n_cams);
+    for (int k = 0; k < n_cams; ++k) table[(size_t)k] = cam_tile(batch, g, k);
+    QB_BCUDA(cudaMemcpyAsync(bat<void>(batch, L.cam_table), table.data(), sizeof(CamTile) * table.size(),
+                             cudaMemcpyHostToDevice, s));
+    QB_BCUDA(cudaStreamSynchronize(s));  // the host table goes out of scope
     return QB_OK;
 }
 
@@ -270,13 +318,17 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         return bfail(QB_ERR_INVALID_ARG, "invalid tuning");
     cudaStream_t s = (cudaStream_t)stream;
     const int n = b->n;
+    const uint64_t cap = b->pair_capacity;
+    const int rb = t.sort_digit_bits;
     uint64_t *npairs = bat<uint64_t>(b, L.state);
-    uint32_t *err = reinterpret_cast<uint32_t *>(bat<uint8_t>(b, L.state) + 8 * (size_t)b->n_groups);
+    uint32_t *err = err_word(b, L);
+    uint32_t *keysA = bat<uint32_t>(b, L.keysA), *keysB = bat<uint32_t>(b, L.keysB);
+    uint32_t *valsT = bat<uint32_t>(b, L.valsT);
+    void *sort_scratch = bat<void>(b, L.sort);
     for (int gi = 0; gi < b->n_groups; ++gi) {
         GroupView v;
         group_view(b, geo, cams, gi, v);
-        const int nrec = v.ncam * n;
-        // ---- preprocess over (camera, Gaussian) records ----
+        // ---- preprocess over the group's (camera, Gaussian) records ----
         PreArgs a;
         std::memset(&a, 0, sizeof(a));
         a.n = n;
@@ -292,6 +344,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         a.mode = base_mode;
         a.clamp3s = (mode & QB_BIN_NO_CLAMP) == 0;
         a.xy = bat<float2>(b, L.xy) + v.rec0;
+        a.shape = bat<float2>(b, L.shape) + v.rec0;
         a.conic_o = bat<float4>(b, L.conic_o) + v.rec0;
         a.rgbd = bat<float4>(b, L.rgbd) + v.rec0;
         a.box = bat<float4>(b, L.box) + v.rec0;
@@ -299,80 +352,82 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         a.meta = bat<int>(b, L.meta) + v.rec0;
         a.counts = bat<uint32_t>(b, L.counts) + v.rec0;
         a.segs = bat<uint4>(b, L.segs);
-        uint32_t *dk0 = bat<uint32_t>(b, L.dk0), *dk1 = bat<uint32_t>(b, L.dk1);
-        uint32_t *dv0 = bat<uint32_t>(b, L.dv0), *dv1 = bat<uint32_t>(b, L.dv1);
-        a.depth_keys = dk0;  // the depth-order sort's keys, written by the preprocess
-        a.depth_vals = dv0;
+        a.depth_keys = bat<uint32_t>(b, L.dk0);  // the depth-order sort's keys and record indices
+        a.depth_vals = bat<uint32_t>(b, L.dv0);
         QB_BCUDA(launch_preprocess(a, scene->sh_degree, s));
-        // ---- depth order of the records, scan in that order ----
-        int passes = 0;
-        if (nrec > 0)
-            QB_BCUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)nrec, nullptr, kDepthBits, kDepthDigitBits, bat<void>(b, L.dsort),
-                                err, s, &passes));
-        const uint32_t *perm = (passes & 1) ? dv1 : dv0;
-        QB_BCUDA(launch_scan(a.counts, perm, nrec, bat<uint32_t>(b, L.offsets), bat<uint64_t>(b, L.scan_part),
-                             npairs + gi, err, s));
-        // ---- QPass emit of (group tile id, record) pairs in depth order,
-        // stable sort on the tile id (every pass writes keys and values), and
-        // the ranges from the sorted tile ids.  The emit writes the buffer
-        // pair from which the last pass lands in (keysA, this group's slot).
-        const PassGeo tg = pass_geo(v.tile_bits, t.sort_digit_bits);
-        const int tpasses = v.tile_bits > 0 ? tg.passes : 0;
-        uint2 *ranges = bat<uint2>(b, L.ranges) + v.tile0;
-        uint32_t *slot = bat<uint32_t>(b, L.slots) + (size_t)gi * b->pair_capacity;
-        uint32_t *valsT = bat<uint32_t>(b, L.valsT);
-        uint32_t *keysA = bat<uint32_t>(b, L.keysA), *keysB = bat<uint32_t>(b, L.keysB);
-        void *sort_scratch = bat<void>(b, L.sort);
-        const bool into_a = tpasses % 2 == 0;
-        EmitArgs e;
-        std::memset(&e, 0, sizeof(e));
-        e.n = nrec;
-        e.n_per_cam = n > 0 ? n : 1;
-        e.perm = perm;
-        e.xy = a.xy;
-        e.box = a.box;
-        e.r3 = a.r3;
-        e.meta = a.meta;
-        e.rgbd = a.rgbd;
-        e.counts = a.counts;
-        e.offsets = bat<uint32_t>(b, L.offsets);
-        e.vals = into_a ? slot : valsT;
-        e.n_pairs = npairs + gi;
-        e.n_pairs_host = UINT64_MAX;
-        e.capacity = b->pair_capacity;
-        e.mode = base_mode;
-        e.clamp3s = a.clamp3s;
-        e.err = err;
-        e.ts = v.ts;
-        e.segs = bat<uint4>(b, L.segs);
-        QB_BCUDA(launch_emit<uint32_t>(e, into_a ? keysA : keysB, s));
-        if (tpasses > 0) {
-            int done = 0;
-            QB_BCUDA(sort_pairs(into_a ? keysA : keysB, into_a ? slot : valsT, into_a ? keysB : keysA,
-                                into_a ? valsT : slot, b->pair_capacity, npairs + gi, v.tile_bits, t.sort_digit_bits,
-                                sort_scratch, err, s, &done, false));
+        // ---- each camera binned like a frame, into its own slot ----
+        for (int c = 0; c < v.ncam; ++c) {
+            const int k = v.k0 + c;
+            const size_t r0 = (size_t)c * n;  // the camera's records within the group
+            uint32_t *dk0 = bat<uint32_t>(b, L.dk0) + r0, *dk1 = bat<uint32_t>(b, L.dk1) + r0;
+            uint32_t *dv0 = bat<uint32_t>(b, L.dv0) + r0, *dv1 = bat<uint32_t>(b, L.dv1) + r0;
+            int passes = 0;
+            if (n > 0)
+                QB_BCUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)n, nullptr, kDepthBits, kDepthDigitBits,
+                                    bat<void>(b, L.dsort), err, s, &passes));
+            const uint32_t *perm = (passes & 1) ? dv1 : dv0;  // group record indices in depth order
+            QB_BCUDA(launch_scan(a.counts, perm, n, bat<uint32_t>(b, L.offsets), bat<uint64_t>(b, L.scan_part),
+                                 npairs + k, err, s));
+            const int ntiles = geo.tx[k] * geo.ty[k];
+            const int tile_bits = bits_for((uint64_t)ntiles);
+            const int tpasses = tile_bits > 0 ? (tile_bits + rb - 1) / rb : 0;
+            uint32_t *slot = bat<uint32_t>(b, L.slots) + (size_t)k * cap;
+            // plain emit into the buffer pair the first pass reads (or the final one)
+            const bool into_a = tpasses == 0 || !pass_writes_a(tpasses, 0);
+            EmitArgs e;
+            std::memset(&e, 0, sizeof(e));
+            e.n = n;
+            e.n_per_cam = n > 0 ? n : 1;
+            e.perm = perm;
+            e.xy = a.xy;
+            e.box = a.box;
+            e.r3 = a.r3;
+            e.meta = a.meta;
+            e.rgbd = a.rgbd;
+            e.counts = a.counts;
+            e.offsets = bat<uint32_t>(b, L.offsets);
+            e.segs = bat<uint4>(b, L.segs);
+            e.vals = into_a ? slot : valsT;
+            e.n_pairs = npairs + k;
+            e.n_pairs_host = UINT64_MAX;
+            e.capacity = cap;
+            e.mode = base_mode;
+            e.clamp3s = a.clamp3s;
+            e.err = err;
+            e.ts = v.ts;
+            QB_BCUDA(launch_emit<uint32_t>(e, into_a ? keysA : keysB, s));
+            // per-tile counts -> the camera's ranges and every pass's bucket
+            // offsets; then the tile sort, whose last pass writes the slot
+            uint2 *ranges = bat<uint2>(b, L.ranges) + geo.tile_base[k];
+            QB_BCUDA(launch_tile_count(into_a ? keysA : keysB, cap, npairs + k, ntiles,
+                                       bat<uint32_t>(b, L.tile_counts), ranges, sort_hist_table(sort_scratch),
+                                       sort_hist_stride(), rb, tile_bits, s));
+            if (tpasses > 0)
+                QB_BCUDA(tile_sort_passes(keysA, slot, keysB, valsT, cap, cap, npairs + k, tile_bits, 0, rb,
+                                          sort_scratch, err, s));
         }
-        QB_BCUDA(launch_ranges<uint32_t>(keysA, b->pair_capacity, npairs + gi, ranges, (int)v.ts.total_tiles, s));
-        // ---- persistent render over the group's tiles ----
-        QB_BCUDA(cudaMemsetAsync(bat<uint32_t>(b, L.queue), 0, 4, s));
-        RenderArgs r;
-        std::memset(&r, 0, sizeof(r));
-        r.ranges = ranges;
-        r.vals = slot;
-        r.xy = a.xy;
-        r.conic_o = a.conic_o;
-        r.rgbd = a.rgbd;
-        for (int c = 0; c < 3; ++c) r.bg[c] = bg ? bg[c] : 0.f;
-        r.img = d_images;
-        r.tfinal = bat<float>(b, L.tfinal);
-        r.ncontrib = bat<int>(b, L.ncontrib);
-        r.neval = bat<int>(b, L.neval);
-        r.ts = v.ts;
-        r.queue = bat<uint32_t>(b, L.queue);
-        r.tiles_per_fetch = t.tiles_per_fetch;
-        r.blocks_per_sm = t.blocks_per_sm;
-        QB_BCUDA(launch_render(r, t.render_batch, s));
     }
+    // ---- one persistent render over every camera's tiles ----
+    QB_BCUDA(cudaMemsetAsync(bat<uint32_t>(b, L.queue), 0, 4, s));
+    RenderArgs r;
+    std::memset(&r, 0, sizeof(r));
+    r.ranges = bat<uint2>(b, L.ranges);
+    r.vals = bat<uint32_t>(b, L.slots);
+    r.xy = bat<float2>(b, L.xy);
+    r.shape = bat<float2>(b, L.shape);
+    r.conic_o = bat<float4>(b, L.conic_o);
+    r.rgbd = bat<float4>(b, L.rgbd);
+    for (int c = 0; c < 3; ++c) r.bg[c] = bg ? bg[c] : 0.f;
+    r.img = d_images;
+    r.tfinal = bat<float>(b, L.tfinal);
+    r.ncontrib = bat<int>(b, L.ncontrib);
+    r.neval = bat<int>(b, L.neval);
+    r.ts = batch_tileset(b, geo);
+    r.cam_table = bat<CamTile>(b, L.cam_table);
+    r.queue = bat<uint32_t>(b, L.queue);
+    r.tiles_per_fetch = t.tiles_per_fetch;
+    r.blocks_per_sm = t.blocks_per_sm;
+    QB_BCUDA(launch_render(r, t.render_batch, s));
     b->sh_degree = scene->sh_degree;
     b->bin_mode = mode;
     b->stage = 1;
@@ -395,30 +450,33 @@ qb_status qb_render_batch_bwd(qb_batch *b, const qb_scene *scene, const qb_camer
         return bfail(QB_ERR_INVALID_ARG, "a gradient array is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const int n = b->n;
+    // ---- one persistent render backward over every camera's tiles ----
+    double *gscreen = bat<double>(b, L.gscreen);
+    QB_BCUDA(cudaMemsetAsync(gscreen, 0, 72 * (size_t)b->n_cams * n, s));
+    QB_BCUDA(cudaMemsetAsync(bat<uint32_t>(b, L.queue), 0, 4, s));
+    BwdArgs r;
+    std::memset(&r, 0, sizeof(r));
+    r.ranges = bat<uint2>(b, L.ranges);
+    r.vals = bat<uint32_t>(b, L.slots);
+    r.xy = bat<float2>(b, L.xy);
+    r.shape = bat<float2>(b, L.shape);
+    r.conic_o = bat<float4>(b, L.conic_o);
+    r.rgbd = bat<float4>(b, L.rgbd);
+    for (int c = 0; c < 3; ++c) r.bg[c] = bg ? bg[c] : 0.f;
+    r.dL_dimg = d_dL_dimages;
+    r.tfinal = bat<float>(b, L.tfinal);
+    r.ncontrib = bat<int>(b, L.ncontrib);
+    r.g_screen = gscreen;
+    r.ts = batch_tileset(b, geo);
+    r.cam_table = bat<CamTile>(b, L.cam_table);
+    r.queue = bat<uint32_t>(b, L.queue);
+    r.tiles_per_fetch = b->reserved[0] > 0 ? b->reserved[0] : 1;
+    r.blocks_per_sm = b->reserved[1];
+    QB_BCUDA(launch_render_bwd(r, s));
+    // ---- the chain to the scene parameters, one launch per group ----
     for (int gi = 0; gi < b->n_groups; ++gi) {
         GroupView v;
         group_view(b, geo, cams, gi, v);
-        const size_t nrec = (size_t)v.ncam * n;
-        double *gscreen = bat<double>(b, L.gscreen);
-        QB_BCUDA(cudaMemsetAsync(gscreen, 0, 72 * nrec, s));
-        QB_BCUDA(cudaMemsetAsync(bat<uint32_t>(b, L.queue), 0, 4, s));
-        BwdArgs r;
-        std::memset(&r, 0, sizeof(r));
-        r.ranges = bat<uint2>(b, L.ranges) + v.tile0;
-        r.vals = bat<uint32_t>(b, L.slots) + (size_t)gi * b->pair_capacity;
-        r.xy = bat<float2>(b, L.xy) + v.rec0;
-        r.conic_o = bat<float4>(b, L.conic_o) + v.rec0;
-        r.rgbd = bat<float4>(b, L.rgbd) + v.rec0;
-        for (int c = 0; c < 3; ++c) r.bg[c] = bg ? bg[c] : 0.f;
-        r.dL_dimg = d_dL_dimages;
-        r.tfinal = bat<float>(b, L.tfinal);
-        r.ncontrib = bat<int>(b, L.ncontrib);
-        r.g_screen = gscreen;
-        r.ts = v.ts;
-        r.queue = bat<uint32_t>(b, L.queue);
-        r.tiles_per_fetch = b->reserved[0] > 0 ? b->reserved[0] : 1;
-        r.blocks_per_sm = b->reserved[1];
-        QB_BCUDA(launch_render_bwd(r, s));
         PreBwdArgs p;
         std::memset(&p, 0, sizeof(p));
         p.n = n;
@@ -430,7 +488,7 @@ qb_status qb_render_batch_bwd(qb_batch *b, const qb_scene *scene, const qb_camer
         p.raw = scene->params_raw != 0;
         p.cams = v.cs;
         p.meta = bat<int>(b, L.meta) + v.rec0;
-        p.g_screen = gscreen;
+        p.g_screen = gscreen + 9 * v.rec0;
         p.gm = grads->means;
         p.gs = grads->scales;
         p.gq = grads->quats;
@@ -451,12 +509,12 @@ qb_status qb_batch_check(qb_batch *b, uint64_t *pairs_out, qb_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t flags = 0;
     uint8_t *state = bat<uint8_t>(b, L.state);
-    QB_BCUDA(cudaMemcpyAsync(&flags, state + 8 * (size_t)b->n_groups, 4, cudaMemcpyDeviceToHost, s));
+    QB_BCUDA(cudaMemcpyAsync(&flags, err_word(b, L), 4, cudaMemcpyDeviceToHost, s));
     if (pairs_out)
-        QB_BCUDA(cudaMemcpyAsync(pairs_out, state, 8 * (size_t)b->n_groups, cudaMemcpyDeviceToHost, s));
+        QB_BCUDA(cudaMemcpyAsync(pairs_out, state, 8 * (size_t)b->n_cams, cudaMemcpyDeviceToHost, s));
     QB_BCUDA(cudaStreamSynchronize(s));
-    if (flags) QB_BCUDA(cudaMemsetAsync(state + 8 * (size_t)b->n_groups, 0, 4, s));
-    if (flags & kErrCapacity) return bfail(QB_ERR_CAPACITY, "a group's pairs exceeded the pair capacity");
+    if (flags) QB_BCUDA(cudaMemsetAsync(err_word(b, L), 0, 4, s));
+    if (flags & kErrCapacity) return bfail(QB_ERR_CAPACITY, "a camera's pairs exceeded the pair capacity");
     if (flags & kErrTimeout) return bfail(QB_ERR_TIMEOUT, "a device spin-wait reached its iteration limit");
     return QB_OK;
 }

@@ -38,7 +38,7 @@ struct CamDev {
 
 // Workspace offsets (bytes) of a frame; all 256-byte aligned.
 struct Layout {
-    size_t xy, conic_o, rgbd, box, r3, meta, counts, offsets, segs;
+    size_t xy, shape, conic_o, rgbd, box, r3, meta, counts, offsets, segs;
     size_t scan_part;
     size_t keys0, keys1, vals0, vals1;
     size_t sort_scratch, sort_scratch_bytes;
@@ -118,6 +118,14 @@ cudaError_t tile_sort_passes(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t 
 inline bool pass_writes_a(int passes, int p) { return ((passes - 1 - p) & 1) == 0; }
 
 // ---- device helpers -----------------------------------------------------------
+// Gaussians whose stretching factor f (Eq. f-closed) has f^2 below this take
+// the render's exact power form: with r = b / a = -Sigma12 / Sigma22 and
+// u = dx + r dy, d^T Lambda d = a u^2 + dy^2 / Sigma22, a sum of two
+// non-negative terms, where a dx^2 + 2 b dx dy + c dy^2 of a thin Gaussian
+// cancels its large terms in float32 (an error of about 2^-24 (a dx^2 +
+// 2 |b dx dy| + c dy^2), up to 10^5 times the result along a needle).
+constexpr float kElongatedF2 = 0.01f;  // f < 0.1: aspect ratio above 10 : 1
+
 // Exponents below this give alpha = o e^power < (1/255) e^-0.001: the 1e-3
 // margin is far wider than the float32 error of the alpha test, so skipping
 // them first never changes a decision of that test.

@@ -23,6 +23,7 @@ struct PreArgs {
     int mode;
     bool clamp3s;
     float2 *xy;      // [n_cams * n] ...
+    float2 *shape;   // (r, -e/2) of an elongated Gaussian's exact power form, else (0, 0)
     float4 *conic_o, *rgbd, *box;
     float *r3;
     int *meta;
@@ -44,12 +45,28 @@ __device__ __forceinline__ int seg_chunks(int ns) { return (1 + 2 * ns + 3) >> 2
 // Image geometry of one camera in a set of cameras rendered together.  Tile
 // ids are global over the set (camera c owns [tile_base, tile_base + tiles));
 // per-pixel arrays and the planar [3][H][W] image of camera c start at pixel
-// pix_base (the image at float offset 3 * pix_base).
+// pix_base (the image at float offset 3 * pix_base).  The render reads the
+// camera's sorted values at vals + vals_base (its ranges are relative to it)
+// and a value v names the record rec_base + v.
 struct CamTile {
     int W, H, tiles_x, tiles_y;
     uint32_t tile_base;
+    uint32_t rec_base;
     uint64_t pix_base;
+    uint64_t vals_base;
 };
+
+// The camera owning global tile t in a device table of n cameras ordered by
+// tile_base (binary search).
+__device__ __forceinline__ int camera_in_table(const CamTile *table, int n, uint32_t t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].tile_base <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 struct TileSet {
     int n_cams;
@@ -94,6 +111,7 @@ struct RenderArgs {
     const uint2 *ranges;  // by global tile
     const uint32_t *vals;
     const float2 *xy;
+    const float2 *shape;
     const float4 *conic_o, *rgbd;
     float bg[3];
     float *img;     // packed planar images
@@ -104,12 +122,15 @@ struct RenderArgs {
     uint32_t *queue;     // persistent launch: tile counter (zeroed); null: one block per tile
     int tiles_per_fetch;
     int blocks_per_sm;   // persistent blocks per SM (0: occupancy limit)
+    unsigned long long *counts;  // measurement only (single frame): [evaluated, power test passed] or null
+    const CamTile *cam_table;    // persistent launch over ts.n_cams cameras from this device table, or null (ts.cam)
 };
 
 struct BwdArgs {
     const uint2 *ranges;
     const uint32_t *vals;
     const float2 *xy;
+    const float2 *shape;
     const float4 *conic_o, *rgbd;
     float bg[3];
     const float *dL_dimg;  // packed like the images
@@ -120,6 +141,7 @@ struct BwdArgs {
     uint32_t *queue;
     int tiles_per_fetch;
     int blocks_per_sm;
+    const CamTile *cam_table;  // as RenderArgs::cam_table
 };
 
 struct PreBwdArgs {

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     if (!ok) {
         a.counts[o] = 0u;
         a.meta[o] = 0;
+        a.shape[o] = make_float2(0.f, 0.f);
         if (a.depth_keys) {  // no tiles: sorts after every Gaussian that has some
             a.depth_keys[o] = 0x7fffffffu;
             a.depth_vals[o] = (uint32_t)o;
@@ -152,6 +153,13 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
     if (a.mode == QB_BIN_QUADBOX_NAIVE) cnt = naive_count(rects);  // the same set, counted the naive way
 
     a.xy[o] = make_float2(p.mx, p.my);
+    // the exact power form's terms (qb_internal.cuh), for elongated Gaussians only
+    float2 shape = make_float2(0.f, 0.f);
+    if (p.det < kElongatedF2 * (p.s11 * p.s22)) {
+        const float inv22 = 1.0f / p.s22;
+        shape = make_float2(-p.s12 * inv22, -0.5f * inv22);
+    }
+    a.shape[o] = shape;
     a.conic_o[o] = make_float4(p.a, p.b, p.c, p.o);
     a.rgbd[o] = make_float4(rgb[0], rgb[1], rgb[2], p.tz);
     a.box[o] = bt.box;

@@ -2,8 +2,11 @@
 // "Render", Eq. 2), as one block per tile (single frame) or as a persistent
 // kernel that takes tiles of several cameras from a global work queue.
 //
-// A tile is rendered by 128 threads, each owning two pixels of one column
-// (rows r and r + 8).  The tile's depth-sorted Gaussian list is walked in
+// A tile is rendered by 64 threads, two warps each owning one half of the
+// tile (rows 0-7 or 8-15); a thread owns four pixels of one column of its
+// half, rows r, r + 2, r + 4 and r + 6, evaluated as two packed pairs (r, r + 2)
+// and (r + 4, r + 6) that share the column's dx terms.  The tile's
+// depth-sorted Gaussian list is walked in
 // batches staged in shared memory (mu^2D, the skip threshold, opacity, the
 // rescaled conic and the colour).  Per entry and pixel (3DGS conventions):
 //   power = -(a dx^2 + 2 b dx dy + c dy^2)/2, skip if power > 0 or if it is
@@ -11,140 +14,225 @@
 //   alpha = min(0.99, o e^power), skip if alpha < 1/255;
 //   T' = T (1 - alpha); stop before adding once T' < 1e-4;
 //   C += alpha T c; T = T'.
-// The thread's two pixels are evaluated together with the packed FP32x2
-// instructions (fma/mul/add .f32x2); each packed lane rounds exactly like
-// the scalar operation it replaces.  A tile ends as soon as all of its
-// pixels have stopped.
+// Each pair is evaluated with the packed FP32x2 instructions (fma/mul/add
+// .f32x2); each packed lane rounds exactly like the scalar operation it
+// replaces.  A tile ends as soon as all of its pixels have stopped.
 #include "qb_kernels.cuh"
 
 namespace qb {
 
-constexpr int kRenderThreads = 128;  // two pixels per thread
+constexpr int kRenderThreads = 64;  // four pixels per thread
+constexpr float kCapTest = 0.98f;    // opacities above this may meet the 0.99 cap
+#define kNaN __int_as_float(0x7fc00000)
+constexpr int kRenderPairs = 2;     // packed pixel pairs per thread
 
 // Per staged entry, five float4 in shared memory laid out for the packed
-// FP32x2 arithmetic of sm_100+: every operand the two pixels of a thread
+// FP32x2 arithmetic of sm_100+: every operand the two pixels of a pair
 // share is stored twice, so a pair register loads it without a move.
 //   sx = (mu_x, mu_x, mu_y, mu_y), sq = (ca, ca, cb, cb),
-//   sk = (cc, cc, skip threshold, opacity), sc1 = (r, r, g, g), sc2 = (b, b, -, -).
+//   sk = (cc, cc, skip threshold, +-opacity), sc1 = (r, r, g, g),
+//   sc2 = (b, b, rr, ce).
+// An elongated Gaussian (qb_internal.cuh) carries a negative opacity and the
+// exact power form's rr = b / a and ce = -1 / (2 Sigma22): its exponent is
+// ca u^2 + ce dy^2 with u = dx + rr dy, which does not cancel.
 struct RenderStage {
     float4 *sx, *sq, *sk, *sc1, *sc2;
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Both pixels of the thread are composited in lock step: every entry's
-// exponent is evaluated for the pair with packed operations; entries whose
-// exponent is out of range for every pixel of the warp skip the rest.  An
-// entry a pixel rejects (or a pixel that has stopped) takes weight 0, which
-// leaves its colour and transmittance bit-for-bit unchanged, so the branch-free
-// update composes exactly the entries the per-pixel rules of the header accept.
-template <int BATCH>
-__device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile, int ci, const RenderStage &S) {
-    const CamTile &C = a.ts.cam[ci];
+// The compositing state of one packed pair of pixels.
+struct RenderPair {
+    float2 T, cr, cg, cb, npy;
+    bool in0, in1, done0, done1;
+    int n0, n1, last0, last1;
+};
+
+// Both pixels of a pair are composited in lock step: every entry's exponent
+// is evaluated for the pair with packed operations; entries whose exponent
+// is out of range for every pixel of the warp skip the rest.  An entry a
+// pixel rejects (or a pixel that has stopped) takes weight 0, which leaves
+// its colour and transmittance bit-for-bit unchanged, so the branch-free
+// update composes exactly the entries the per-pixel rules of the header
+// accept.
+// COUNT (measurement only) also adds the tile's (pixel, entry) evaluations
+// and the evaluations whose power test passed to a.counts[0], a.counts[1].
+template <int BATCH, bool COUNT = false>
+__device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile, const CamTile &C, const RenderStage &S) {
     const uint32_t lt = gtile - C.tile_base;
+    const uint32_t *vals = a.vals + C.vals_base;
     const int tx = (int)(lt % (uint32_t)C.tiles_x), ty = (int)(lt / (uint32_t)C.tiles_x);
-    const int tid = threadIdx.x;
-    const int px = tx * kTile + (tid & (kTile - 1));
-    const int py0 = ty * kTile + (tid >> kTileShift), py1 = py0 + 8;
-    const bool in0 = px < C.W && py0 < C.H, in1 = px < C.W && py1 < C.H;
-    const float2 npx = f2(-(float)px, -(float)px), npy = f2(-(float)py0, -(float)py1);
-    bool done0 = !in0, done1 = !in1;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int px = tx * kTile + (lane & (kTile - 1));
+    const int pyb = ty * kTile + wid * 8 + (lane >> kTileShift);
+    const float2 npx = f2(-(float)px, -(float)px);
+    RenderPair P[kRenderPairs];
+#pragma unroll
+    for (int r = 0; r < kRenderPairs; ++r) {
+        const int y0 = pyb + 4 * r, y1 = y0 + 2;
+        P[r].in0 = px < C.W && y0 < C.H;
+        P[r].in1 = px < C.W && y1 < C.H;
+        P[r].done0 = !P[r].in0;
+        P[r].done1 = !P[r].in1;
+        // a pixel outside the image (later: one that has stopped) carries a
+        // NaN row, so its exponent is NaN and fails every test
+        P[r].npy = f2(P[r].in0 ? -(float)y0 : kNaN, P[r].in1 ? -(float)y1 : kNaN);
+        P[r].T = f2(1.f, 1.f);
+        P[r].cr = P[r].cg = P[r].cb = f2(0.f, 0.f);
+        P[r].n0 = P[r].n1 = P[r].last0 = P[r].last1 = 0;
+    }
+    auto all_done = [&]() {
+        bool d = true;
+#pragma unroll
+        for (int r = 0; r < kRenderPairs; ++r) d = d && P[r].done0 && P[r].done1;
+        return d;
+    };
 
     const uint2 range = a.ranges[gtile];
     const int total = (int)(range.y - range.x);
-    float2 T = f2(1.f, 1.f), cr = f2(0.f, 0.f), cg = f2(0.f, 0.f), cb = f2(0.f, 0.f);
-    int n0 = 0, n1 = 0, last0 = 0, last1 = 0;
+    uint32_t npass = 0;  // COUNT only
 
     for (int base = 0; base < total; base += BATCH) {
-        if (__syncthreads_count(done0 && done1) == kRenderThreads) break;
+        if (__syncthreads_count(all_done()) == kRenderThreads) break;
         for (int q = tid; q < BATCH; q += kRenderThreads) {
             const int idx = base + q;
             if (idx < total) {
-                const uint32_t g = a.vals[range.x + idx];
+                const uint32_t g = C.rec_base + vals[range.x + idx];
                 const float2 m = a.xy[g];
                 const float4 co = a.conic_o[g];
                 const float4 rgb = a.rgbd[g];
+                const float2 sh = a.shape[g];
                 const float ca = -0.5f * co.x, cbv = -co.y, cc = -0.5f * co.z;
                 S.sx[q] = make_float4(m.x, m.x, m.y, m.y);
                 S.sq[q] = make_float4(ca, ca, cbv, cbv);
-                S.sk[q] = make_float4(cc, cc, skip_threshold(co.w), co.w);
+                S.sk[q] = make_float4(cc, cc, skip_threshold(co.w), sh.y != 0.f ? -co.w : co.w);
                 S.sc1[q] = make_float4(rgb.x, rgb.x, rgb.y, rgb.y);
-                S.sc2[q] = make_float4(rgb.z, rgb.z, 0.f, 0.f);
+                S.sc2[q] = make_float4(rgb.z, rgb.z, sh.x, sh.y);
             }
         }
         __syncthreads();
         const int cnt = min(BATCH, total - base);
         for (int j = 0; j < cnt; ++j) {
             // every 32 entries: leave once all pixels of the warp have stopped
-            if ((j & 31) == 0 && __all_sync(0xffffffffu, done0 && done1)) break;
+            if ((j & 31) == 0 && __all_sync(0xffffffffu, all_done())) break;
             const float4 X = S.sx[j], Q = S.sq[j], K = S.sk[j];
-            // power = A + dy (B + cc dy), A = ca dx^2, B = cb dx (the operation
-            // sequence of power_terms / power_from, per pixel)
             const float2 dx = __fadd2_rn(f2(X.x, X.y), npx);
-            const float2 A = __fmul2_rn(__fmul2_rn(f2(Q.x, Q.y), dx), dx);
-            const float2 B = __fmul2_rn(f2(Q.z, Q.w), dx);
-            const float2 dy = __fadd2_rn(f2(X.z, X.w), npy);
-            const float2 pw = __ffma2_rn(dy, __ffma2_rn(f2(K.x, K.y), dy, B), A);
-            const bool e0 = !done0 && pw.x <= 0.f && pw.x >= K.z;
-            const bool e1 = !done1 && pw.y <= 0.f && pw.y >= K.z;
-            if (!__any_sync(0xffffffffu, e0 || e1)) continue;
-            const float a0 = fminf(kAlphaMax, __fmul_rn(K.w, __expf(pw.x)));
-            const float a1 = fminf(kAlphaMax, __fmul_rn(K.w, __expf(pw.y)));
-            const bool ok0 = e0 && a0 >= kAlphaMin, ok1 = e1 && a1 >= kAlphaMin;
-            // T (1 - alpha); fma(alpha, -1, 1) is 1 - alpha rounded once
-            const float2 tT = __fmul2_rn(T, __ffma2_rn(f2(a0, a1), f2(-1.f, -1.f), f2(1.f, 1.f)));
-            const bool st0 = ok0 && tT.x < kTStop, st1 = ok1 && tT.y < kTStop;
-            const bool ac0 = ok0 && !st0, ac1 = ok1 && !st1;
+            float2 pw[kRenderPairs];
+            if (K.w >= 0.f) {
+                // power = A + dy (B + cc dy), A = ca dx^2, B = cb dx; dx, A and
+                // B are the column's, shared by the thread's four pixels
+                const float2 A = __fmul2_rn(__fmul2_rn(f2(Q.x, Q.y), dx), dx);
+                const float2 B = __fmul2_rn(f2(Q.z, Q.w), dx);
+#pragma unroll
+                for (int r = 0; r < kRenderPairs; ++r) {
+                    const float2 dy = __fadd2_rn(f2(X.z, X.w), P[r].npy);
+                    pw[r] = __ffma2_rn(dy, __ffma2_rn(f2(K.x, K.y), dy, B), A);
+                }
+            } else {
+                // elongated (the same for the whole warp): power = ca u^2 +
+                // ce dy^2, u = dx + rr dy
+                const float4 E = S.sc2[j];
+#pragma unroll
+                for (int r = 0; r < kRenderPairs; ++r) {
+                    const float2 dy = __fadd2_rn(f2(X.z, X.w), P[r].npy);
+                    const float2 u = __ffma2_rn(f2(E.z, E.z), dy, dx);
+                    pw[r] = __ffma2_rn(__fmul2_rn(f2(Q.x, Q.y), u), u, __fmul2_rn(__fmul2_rn(f2(E.w, E.w), dy), dy));
+                }
+            }
+            const float op = fabsf(K.w);
+            const float2 nsk = f2(-K.z, -K.z);
+            bool e0[kRenderPairs], e1[kRenderPairs];
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < kRenderPairs; ++r) {
+                // skip < power <= 0 as one sign test: power (power - skip) <= 0
+                // (skip < 0; the signs of a difference and a product are exact)
+                const float2 t = __fmul2_rn(pw[r], __fadd2_rn(pw[r], nsk));
+                e0[r] = t.x <= 0.f;
+                e1[r] = t.y <= 0.f;
+                if (COUNT) npass += (uint32_t)e0[r] + (uint32_t)e1[r];
+                any = any || e0[r] || e1[r];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const float4 C1 = S.sc1[j], C2 = S.sc2[j];
             // entries evaluated so far by a pixel still running: base + j + 1
             const int nj = base + j + 1;
-            if (st0) n0 = nj;
-            if (st1) n1 = nj;
-            done0 = done0 || st0;
-            done1 = done1 || st1;
-            // alpha of the accepted entries, 0 elsewhere: T (1 - 0) = T and
-            // c + r * 0 = c exactly, so the updates need no select
-            const float2 aa = f2(ac0 ? a0 : 0.f, ac1 ? a1 : 0.f);
-            const float2 w = __fmul2_rn(aa, T);
-            const float4 C1 = S.sc1[j], C2 = S.sc2[j];
-            cr = __ffma2_rn(f2(C1.x, C1.y), w, cr);
-            cg = __ffma2_rn(f2(C1.z, C1.w), w, cg);
-            cb = __ffma2_rn(f2(C2.x, C2.y), w, cb);
-            T = __fmul2_rn(T, __ffma2_rn(aa, f2(-1.f, -1.f), f2(1.f, 1.f)));
-            last0 = ac0 ? nj : last0;
-            last1 = ac1 ? nj : last1;
+            // o G can reach the 0.99 cap only for o near it (G <= 1 up to
+            // the exponential's rounding); the same for the whole warp
+            const bool capped = op > kCapTest;
+#pragma unroll
+            for (int r = 0; r < kRenderPairs; ++r) {
+                RenderPair &q = P[r];
+                float2 al = __fmul2_rn(f2(op, op), f2(__expf(pw[r].x), __expf(pw[r].y)));
+                if (capped) al = f2(fminf(kAlphaMax, al.x), fminf(kAlphaMax, al.y));
+                const float a0 = al.x, a1 = al.y;
+                const bool ok0 = e0[r] && a0 >= kAlphaMin, ok1 = e1[r] && a1 >= kAlphaMin;
+                // T (1 - alpha); fma(alpha, -1, 1) is 1 - alpha rounded once
+                const float2 tT = __fmul2_rn(q.T, __ffma2_rn(al, f2(-1.f, -1.f), f2(1.f, 1.f)));
+                const bool st0 = ok0 && tT.x < kTStop, st1 = ok1 && tT.y < kTStop;
+                const bool ac0 = ok0 && !st0, ac1 = ok1 && !st1;
+                if (st0 || st1) {  // once in a pixel's life: record the stop, poison its row
+                    if (st0) q.n0 = nj, q.done0 = true, q.npy.x = kNaN;
+                    if (st1) q.n1 = nj, q.done1 = true, q.npy.y = kNaN;
+                }
+                // alpha of the accepted entries, 0 elsewhere: T (1 - 0) = T and
+                // c + r * 0 = c exactly, so the updates need no select
+                const float2 aa = f2(ac0 ? a0 : 0.f, ac1 ? a1 : 0.f);
+                const float2 w = __fmul2_rn(aa, q.T);
+                q.cr = __ffma2_rn(f2(C1.x, C1.y), w, q.cr);
+                q.cg = __ffma2_rn(f2(C1.z, C1.w), w, q.cg);
+                q.cb = __ffma2_rn(f2(C2.x, C2.y), w, q.cb);
+                q.T = __fmul2_rn(q.T, __ffma2_rn(aa, f2(-1.f, -1.f), f2(1.f, 1.f)));
+                q.last0 = ac0 ? nj : q.last0;
+                q.last1 = ac1 ? nj : q.last1;
+            }
         }
     }
-    // a pixel that never stopped evaluated the whole list
-    if (!done0) n0 = total;
-    if (!done1) n1 = total;
     const size_t plane = (size_t)C.W * C.H;
     float *img = a.img + 3 * C.pix_base;
-    if (in0) {
-        const size_t pix = (size_t)py0 * C.W + px;
-        img[pix] = fmaf(T.x, a.bg[0], cr.x);
-        img[plane + pix] = fmaf(T.x, a.bg[1], cg.x);
-        img[2 * plane + pix] = fmaf(T.x, a.bg[2], cb.x);
-        a.tfinal[C.pix_base + pix] = T.x;
-        a.ncontrib[C.pix_base + pix] = last0;
-        a.neval[C.pix_base + pix] = n0;
+    unsigned long long ev = 0;
+#pragma unroll
+    for (int r = 0; r < kRenderPairs; ++r) {
+        RenderPair &q = P[r];
+        // a pixel that never stopped evaluated the whole list
+        if (!q.done0) q.n0 = total;
+        if (!q.done1) q.n1 = total;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const bool in = h ? q.in1 : q.in0;
+            if (!in) continue;
+            const int py = pyb + 4 * r + 2 * h;
+            const size_t pix = (size_t)py * C.W + px;
+            const float T = h ? q.T.y : q.T.x;
+            img[pix] = fmaf(T, a.bg[0], h ? q.cr.y : q.cr.x);
+            img[plane + pix] = fmaf(T, a.bg[1], h ? q.cg.y : q.cg.x);
+            img[2 * plane + pix] = fmaf(T, a.bg[2], h ? q.cb.y : q.cb.x);
+            a.tfinal[C.pix_base + pix] = T;
+            a.ncontrib[C.pix_base + pix] = h ? q.last1 : q.last0;
+            a.neval[C.pix_base + pix] = h ? q.n1 : q.n0;
+            ev += (unsigned long long)(h ? q.n1 : q.n0);
+        }
     }
-    if (in1) {
-        const size_t pix = (size_t)py1 * C.W + px;
-        img[pix] = fmaf(T.y, a.bg[0], cr.y);
-        img[plane + pix] = fmaf(T.y, a.bg[1], cg.y);
-        img[2 * plane + pix] = fmaf(T.y, a.bg[2], cb.y);
-        a.tfinal[C.pix_base + pix] = T.y;
-        a.ncontrib[C.pix_base + pix] = last1;
-        a.neval[C.pix_base + pix] = n1;
+    if (COUNT) {
+        unsigned long long ps = npass;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ev += __shfl_xor_sync(0xffffffffu, ev, o);
+            ps += __shfl_xor_sync(0xffffffffu, ps, o);
+        }
+        if (lane == 0) {
+            atomicAdd(a.counts, ev);
+            atomicAdd(a.counts + 1, ps);
+        }
     }
 }
 
 // One block per tile of a single camera.
-template <int BATCH>
+template <int BATCH, bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads) render_kernel(RenderArgs a) {
     __shared__ float4 s_stage[5][BATCH];
     const RenderStage S{s_stage[0], s_stage[1], s_stage[2], s_stage[3], s_stage[4]};
-    render_tile<BATCH>(a, blockIdx.x, 0, S);
+    render_tile<BATCH, COUNT>(a, blockIdx.x, a.ts.cam[0], S);
 }
 
 // Persistent blocks take tiles_per_fetch consecutive tiles at a time from a
@@ -161,7 +249,14 @@ __global__ void __launch_bounds__(kRenderThreads) render_persistent_kernel(Rende
         __syncthreads();
         if (t0 >= a.ts.total_tiles) break;
         const uint32_t t1 = min(t0 + (uint32_t)a.tiles_per_fetch, a.ts.total_tiles);
-        for (uint32_t t = t0; t < t1; ++t) render_tile<BATCH>(a, t, camera_of(a.ts, t), S);
+        for (uint32_t t = t0; t < t1; ++t) {
+            if (a.cam_table) {
+                const CamTile C = a.cam_table[camera_in_table(a.cam_table, a.ts.n_cams, t)];
+                render_tile<BATCH>(a, t, C, S);
+            } else {
+                render_tile<BATCH>(a, t, a.ts.cam[camera_of(a.ts, t)], S);
+            }
+        }
     }
 }
 
@@ -174,8 +269,11 @@ static cudaError_t launch_render_b(const RenderArgs &a, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<BATCH>, kRenderThreads, 0);
         if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
         note_launch("render_persistent_kernel", s), render_persistent_kernel<BATCH><<<sms * (per_sm > 0 ? per_sm : 1), kRenderThreads, 0, s>>>(a);
+    } else if (a.counts) {
+        note_launch("render_kernel_counted", s),
+            render_kernel<BATCH, true><<<a.ts.total_tiles, kRenderThreads, 0, s>>>(a);
     } else {
-        note_launch("render_kernel", s), render_kernel<BATCH><<<a.ts.total_tiles, kRenderThreads, 0, s>>>(a);
+        note_launch("render_kernel", s), render_kernel<BATCH, false><<<a.ts.total_tiles, kRenderThreads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -252,9 +252,9 @@ def tune_struct(tune=None) -> N.QbTune:
 class Batch:
     """Many cameras of one scene rendered with the batched entry points.
 
-    Cameras are processed in groups of `group`; `pair_capacity` bounds the
-    Gaussian-tile pairs of one group (see calibrate()).  Images are packed in
-    one buffer; image(k) is camera k's [3, H, W] view."""
+    The preprocess runs per group of `group` cameras; `pair_capacity` bounds
+    the Gaussian-tile pairs of one camera (see calibrated_batch()).  Images
+    are packed in one buffer; image(k) is camera k's [3, H, W] view."""
 
     def __init__(self, n, cams, group=16, pair_capacity=None, device="cuda", stream=None):
         self.n = int(n)
@@ -263,7 +263,7 @@ class Batch:
         self.group = int(min(group, N.QB_GROUP_MAX, len(cams)))
         if pair_capacity is None:
             tiles = max(((w + 15) // 16) * ((h + 15) // 16) for w, h in zip(self.widths, self.heights))
-            pair_capacity = min(2 ** 30, self.group * max(8 * self.n, 4 * tiles))
+            pair_capacity = min(2 ** 30, max(8 * self.n, 4 * tiles))
         self.pair_capacity = int(pair_capacity)
         self.device = device
         self.stream = stream
@@ -301,7 +301,7 @@ class Batch:
 
 def calibrated_batch(scene, cams, mode="quadbox", group=16, headroom=1.1, tune=None):
     """A Batch whose pair capacity fits this scene and these cameras: one
-    render with a generous capacity measures the pairs of every group."""
+    render with a generous capacity measures the pairs of every camera."""
     scene_s, cams_arr = scene_struct(scene), camera_array(cams)
     n = scene_s.n
     probe = Batch(n, cams, group, pair_capacity=None)

@@ -62,12 +62,12 @@ def test_capacity_guess_bounds():
 
 
 def test_kernel_work_figures():
-    P, n, E = 34_613_290, 1_000_000, 123_456_789
-    w = bench.kernel_work(P, n, E)
+    P, n, E, Ep = 34_613_290, 1_000_000, 123_456_789, 23_456_789
+    w = bench.kernel_work(P, n, (E, Ep))
     assert w["tile_sort_pass"] == ("hbm", 16 * P)
     assert w["tile_sort_pass_values"] == ("hbm", 12 * P)
     assert w["emit_warp_kernel"] == ("hbm", 8 * P + 28 * n)
-    assert w["render_kernel"] == ("alu", E * bench.RENDER_FLOPS_PER_EVAL)
+    assert w["render_kernel"] == ("alu", 9 * E + 12 * Ep)  # power test on every entry, alpha and blend on passes
     assert w["preprocess_kernel"] == ("hbm", n * bench.PREPROCESS_BYTES)
     # every captured kernel's traffic refers to a kernel with algorithmic work
     assert set(bench.TRAFFIC_PER_UNIT) <= set(w)
@@ -85,11 +85,12 @@ def test_roofline_picks_the_dominant_kernel_and_uses_the_measured_peaks():
         "not_a_kernel_of_ours": {"ms_per_launch": 9.0, "ms_per_step": 9.0},
     }
     clk = {"sm_mhz": 2000.0}
-    r = bench.roofline({}, kernels, P, n, 1920, 1080, 8, E, clk, "depth_first", sms=148)
+    Ep = 100_000_000
+    r = bench.roofline({}, kernels, P, n, 1920, 1080, 8, (E, Ep), clk, "depth_first", sms=148)
     assert r["kernel"] == "render_kernel" and r["bound"] == "alu"
     alu_peak = 148 * 128 * 2 * 2000.0 * 1e6 / 1e12  # the SM count passed in, not a constant
     assert r["peak"] == pytest.approx(alu_peak, rel=1e-3)
-    assert r["achieved"] == pytest.approx(E * bench.RENDER_FLOPS_PER_EVAL / 0.30e-3 / 1e12, rel=1e-3)
+    assert r["achieved"] == pytest.approx((9 * E + 12 * Ep) / 0.30e-3 / 1e12, rel=1e-3)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
     unit, per = bench.TRAFFIC_PER_UNIT["render_kernel"]
     assert unit == "eval" and r["traffic"] == int(per * E)

@@ -626,3 +626,12 @@ def test_pixel_subset_backward_equals_the_masked_full_backward():
     for a, b in zip(full, sub):
         assert np.any(a != 0)
         np.testing.assert_array_equal(a, b)
+    # the magnitude sums bound the gradients (triangle inequality), and with
+    # a non-negative dL every colour term is non-negative, so there they agree
+    g, mag = O.render_backward_pixels(W, H, pxs, pys, G[:, pys, pxs].T, L["ranges"], L["vals"], proj,
+                                      bg=(0.1, 0.2, 0.3), magnitudes=True)
+    for a, m in zip(g, mag):
+        assert np.all(np.abs(a) <= m * (1 + 1e-12))
+    gp, magp = O.render_backward_pixels(W, H, pxs, pys, np.abs(G[:, pys, pxs].T), L["ranges"], L["vals"], proj,
+                                        magnitudes=True)
+    np.testing.assert_allclose(gp[3], magp[3], rtol=1e-12)
