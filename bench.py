@@ -865,8 +865,8 @@ def run_reference(args):
 
 # Sections of the full result printed on their own lines before the headline
 # (and kept whole in the --out file).
-DETAIL_SECTIONS = ("kernels_fwd", "roofline_kernels", "quadbox_other_sort_modes", "autotune", "c4_fwd_bwd",
-                   "binning_modes", "c3_zoom", "batch64", "cpu_baseline_detail")
+DETAIL_SECTIONS = ("kernels_fwd", "roofline_kernels", "render_work", "quadbox_other_sort_modes", "autotune",
+                   "c4_fwd_bwd", "binning_modes", "c3_zoom", "batch64", "cpu_baseline")
 
 HEADLINE_MAX_BYTES = 2000
 

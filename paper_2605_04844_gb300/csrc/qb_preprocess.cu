@@ -11,7 +11,7 @@
 namespace qb {
 
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a) {
+__global__ void __launch_bounds__(256, 3) preprocess_kernel(PreArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int ci = blockIdx.y;  // camera of this grid row
