@@ -58,6 +58,8 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     L.meta = take(4 * N);
     L.counts = take(4 * N);
     L.offsets = take(4 * N);
+    L.counts_e = take(4 * N);
+    L.chunk_first = take(4 * chunk_table_size(cap));
     L.segs = take(64 * N);
     L.scan_part = take(8 * scan_partials_count(n));
     L.keys0 = take(8 * cap);
@@ -392,7 +394,8 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
         perm = frame->depth_in_alt ? dv1 : dv0;
     }
     QB_CUDA(launch_scan(at<uint32_t>(frame, L.counts), perm, frame->n, at<uint32_t>(frame, L.offsets),
-                        at<uint64_t>(frame, L.scan_part), d_np, err, s));
+                        at<uint64_t>(frame, L.scan_part), d_np, err, s, at<uint32_t>(frame, L.counts_e),
+                        at<uint32_t>(frame, L.chunk_first), (uint32_t)chunk_table_size(frame->pair_capacity)));
     if (eff == QB_SORT_DEPTH_FIRST && fused) {
         // per-tile counts -> ranges and the tile sort's bucket offsets
         const int tile_bits = frame->key_bits - kDepthBits;
@@ -430,6 +433,8 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     a.rgbd = at<float4>(frame, L.rgbd);
     a.counts = at<uint32_t>(frame, L.counts);
     a.offsets = at<uint32_t>(frame, L.offsets);
+    a.counts_e = at<uint32_t>(frame, L.counts_e);
+    a.chunk_first = at<uint32_t>(frame, L.chunk_first);
     a.vals = at<uint32_t>(frame, L.vals0);
     a.n_pairs = d_np;
     a.n_pairs_host = frame->n_pairs;

@@ -79,7 +79,7 @@ struct BLayout {
     size_t tfinal, ncontrib, neval;                   // [total pixels]
     size_t segs, dk0, dk1, dv0, dv1;                  // [group * n] group scratch
     size_t keysA, keysB, valsT;                       // [cap] one camera's pair scratch
-    size_t offsets, scan_part, dsort, sort, tile_counts;
+    size_t offsets, counts_e, chunk_first, scan_part, dsort, sort, tile_counts;
     size_t gscreen;                                   // [n_cams * n][9]
     size_t queue, state;
     size_t total;
@@ -118,6 +118,8 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
     L.keysB = take(4 * cap);
     L.valsT = take(4 * cap);
     L.offsets = take(4 * (size_t)n);
+    L.counts_e = take(4 * (size_t)n);
+    L.chunk_first = take(4 * chunk_table_size(cap));
     L.scan_part = take(8 * scan_partials_count(n));
     size_t db = 0, sb = 0;
     for (int d = 8; d <= kMaxDigitBits; ++d) {
@@ -367,7 +369,8 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
                                     bat<void>(b, L.dsort), err, s, &passes));
             const uint32_t *perm = (passes & 1) ? dv1 : dv0;  // group record indices in depth order
             QB_BCUDA(launch_scan(a.counts, perm, n, bat<uint32_t>(b, L.offsets), bat<uint64_t>(b, L.scan_part),
-                                 npairs + k, err, s));
+                                 npairs + k, err, s, bat<uint32_t>(b, L.counts_e), bat<uint32_t>(b, L.chunk_first),
+                                 (uint32_t)chunk_table_size(cap)));
             const int ntiles = geo.tx[k] * geo.ty[k];
             const int tile_bits = bits_for((uint64_t)ntiles);
             const int tpasses = tile_bits > 0 ? (tile_bits + rb - 1) / rb : 0;
@@ -386,6 +389,8 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
             e.rgbd = a.rgbd;
             e.counts = a.counts;
             e.offsets = bat<uint32_t>(b, L.offsets);
+            e.counts_e = bat<uint32_t>(b, L.counts_e);
+            e.chunk_first = bat<uint32_t>(b, L.chunk_first);
             e.segs = bat<uint4>(b, L.segs);
             e.vals = into_a ? slot : valsT;
             e.n_pairs = npairs + k;

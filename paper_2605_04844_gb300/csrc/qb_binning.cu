@@ -68,10 +68,17 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Besides the offsets it can write the counts in emission order (counts_e)
+// and, for every run of kEmitStride output positions starting at c
+// kEmitStride, the emission position whose pairs hold that start
+// (chunk_first[c], c < chunk_cap), so the emit's warps find their first
+// Gaussian with one load instead of a search.
 __global__ void __launch_bounds__(kScanBlock) scan_onepass_kernel(const uint32_t *__restrict__ counts,
                                                                   const uint32_t *__restrict__ perm, int n,
                                                                   uint32_t *__restrict__ offsets, uint64_t *status,
-                                                                  uint32_t *counter, uint64_t *n_pairs, uint32_t *err) {
+                                                                  uint32_t *counter, uint64_t *n_pairs, uint32_t *err,
+                                                                  uint32_t *__restrict__ counts_e,
+                                                                  uint32_t *__restrict__ chunk_first, uint32_t chunk_cap) {
     __shared__ uint32_t s_block;
     __shared__ uint64_t s_prefix;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -143,6 +150,29 @@ __global__ void __launch_bounds__(kScanBlock) scan_onepass_kernel(const uint32_t
     }
     __syncthreads();
     uint64_t run = s_prefix + incl - sum;
+    if (chunk_first) {
+        uint64_t r = run;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (c[k] > 0u) {
+                // the run starts [r, r + c) of this Gaussian that begin a chunk
+                const uint64_t c0 = (r + kEmitStride - 1) / kEmitStride, c1 = (r + c[k] - 1) / kEmitStride;
+                for (uint64_t ch = c0; ch <= c1 && ch < chunk_cap; ++ch) chunk_first[ch] = (uint32_t)(base + k);
+            }
+            r += c[k];
+        }
+    }
+    if (counts_e) {
+        if (base + kScanItems <= (size_t)n) {
+#pragma unroll
+            for (int q = 0; q < kScanItems / 4; ++q)
+                reinterpret_cast<uint4 *>(counts_e + base)[q] = make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k)
+                if (base + k < (size_t)n) counts_e[base + k] = c[k];
+        }
+    }
     if (base + kScanItems <= (size_t)n) {
         uint32_t o[kScanItems];
 #pragma unroll
@@ -166,13 +196,15 @@ __global__ void __launch_bounds__(kScanBlock) scan_onepass_kernel(const uint32_t
 size_t scan_partials_count(int n) { return (size_t)((n + kScanChunk - 1) / kScanChunk) + 1; }
 
 cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uint32_t *offsets, uint64_t *partials,
-                        uint64_t *n_pairs, uint32_t *err, cudaStream_t s) {
+                        uint64_t *n_pairs, uint32_t *err, cudaStream_t s, uint32_t *counts_e, uint32_t *chunk_first,
+                        uint32_t chunk_cap) {
     if (n == 0) return cudaMemsetAsync(n_pairs, 0, sizeof(uint64_t), s);
     const int nb = (n + kScanChunk - 1) / kScanChunk;
     cudaError_t e = cudaMemsetAsync(partials, 0, ((size_t)nb + 1) * sizeof(uint64_t), s);
     if (e != cudaSuccess) return e;
     note_launch("scan_onepass_kernel", s), scan_onepass_kernel<<<nb, kScanBlock, 0, s>>>(
-        counts, perm, n, offsets, partials, reinterpret_cast<uint32_t *>(partials + nb), n_pairs, err);
+        counts, perm, n, offsets, partials, reinterpret_cast<uint32_t *>(partials + nb), n_pairs, err, counts_e,
+        chunk_first, chunk_cap);
     return cudaGetLastError();
 }
 
@@ -197,6 +229,7 @@ __device__ __forceinline__ uint32_t lanemask_le() {
 constexpr int kEmitWarps = 4;  // warps per block (8 measured 0.7 % slower on the forward)
 constexpr int kSegPerWarp = 32 * 7;
 constexpr uint32_t kEmitChunk = 1024;  // output positions per warp (512, 2048, 4096 measured slower)
+static_assert(kEmitChunk % kEmitStride == 0, "a warp's range starts on the scan's chunk table");
 
 // One warp's table of QPass segments for a batch of 32 Gaussians.
 struct SegTable {
@@ -222,8 +255,10 @@ struct SegTable {
 template <typename KeyOut, class Sink>
 __device__ __forceinline__ void emit_range(const EmitArgs &a, uint64_t C, int32_t L, SegTable &S, Sink &&sink) {
     const int lane = threadIdx.x & 31;
-    // last emission position j with offsets[j] <= C (offsets are non-decreasing)
+    // last emission position j with offsets[j] <= C (offsets are non-decreasing):
+    // from the scan's table when it wrote one (C is a multiple of the stride)
     int64_t lo = 0, hi = a.n - 1;  // invariant: offsets[lo] <= C, answer in [lo, hi]
+    if (a.chunk_first) lo = hi = a.chunk_first[C / kEmitStride];
     while (hi > lo) {
         const int64_t span = hi - lo;
         const int64_t probe = lo + (span * (lane + 1) + 31) / 32;  // 32 probes in (lo, hi]
@@ -247,7 +282,7 @@ __device__ __forceinline__ void emit_range(const EmitArgs &a, uint64_t C, int32_
         int64_t rel = (int64_t)1 << 40;
         if (j < a.n) {
             gid = a.perm ? a.perm[j] : (uint32_t)j;
-            cnt = a.counts[gid];
+            cnt = a.counts_e ? a.counts_e[j] : a.counts[gid];
             rel = (int64_t)a.offsets[j] - (int64_t)C;
         }
         const bool relevant = cnt > 0u && rel < L && rel + (int64_t)cnt > 0;

@@ -39,6 +39,7 @@ struct CamDev {
 // Workspace offsets (bytes) of a frame; all 256-byte aligned.
 struct Layout {
     size_t xy, shape, conic_o, rgbd, box, r3, meta, counts, offsets, segs;
+    size_t counts_e, chunk_first;  // counts in emission order; the emit's chunk table
     size_t scan_part;
     size_t keys0, keys1, vals0, vals1;
     size_t sort_scratch, sort_scratch_bytes;

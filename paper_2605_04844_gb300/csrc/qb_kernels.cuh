@@ -96,6 +96,8 @@ struct EmitArgs {
     const float4 *rgbd;
     const uint32_t *counts;   // by Gaussian
     const uint32_t *offsets;  // by emission position
+    const uint32_t *counts_e;     // the counts by emission position, or null (read through perm)
+    const uint32_t *chunk_first;  // emission position holding output position c kEmitStride, or null
     const uint4 *segs;        // QPass segment records from the preprocess, or null (recomputed)
     uint32_t *vals;
     const uint64_t *n_pairs;
@@ -160,7 +162,12 @@ cudaError_t launch_preprocess(const PreArgs &a, int deg, cudaStream_t s);
 // the block counter), cleared by the launch; a look-back that waits too long
 // raises kErrTimeout in *err.
 cudaError_t launch_scan(const uint32_t *counts, const uint32_t *perm, int n, uint32_t *offsets, uint64_t *partials,
-                        uint64_t *n_pairs, uint32_t *err, cudaStream_t s);
+                        uint64_t *n_pairs, uint32_t *err, cudaStream_t s, uint32_t *counts_e = nullptr,
+                        uint32_t *chunk_first = nullptr, uint32_t chunk_cap = 0);
+// Output positions per entry of the scan's chunk table (a divisor of every
+// emit kernel's per-warp output range).
+constexpr uint32_t kEmitStride = 256;
+inline uint64_t chunk_table_size(uint64_t pair_capacity) { return pair_capacity / kEmitStride + 1; }
 size_t scan_partials_count(int n);
 template <typename KeyT>
 cudaError_t launch_emit(const EmitArgs &a, KeyT *keys, cudaStream_t s);
