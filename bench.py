@@ -417,9 +417,9 @@ def kernel_work(P, n, evals):
 # (20,633,099 pairs, 398,728,138 evaluations) summarised under profiles/,
 # scaled to a launch of this frame by its units; valid for the kernels as
 # captured (kernel -> (unit, bytes per unit)).  A kernel changed since its
-# capture has no entry (the emit: its block shape changed afterwards).
+# capture has no entry.
 TRAFFIC_PER_UNIT = {
-    "render_kernel": ("eval", (12.206848e6 + 1.605376e6) / 398728138),
+    "render_kernel": ("eval", (12.994304e6 + 1.490944e6) / 398728138),
     "tile_sort_pass": ("pair", (166.163712e6 + 120.412416e6) / 20633099),
     "tile_sort_pass_values": ("pair", (165.441280e6 + 31.980032e6) / 20633099),
     "tile_count_kernel": ("pair", (82.601216e6 + 1.472768e6) / 20633099),
