@@ -373,12 +373,19 @@ typedef struct {
 size_t qb_batch_workspace_bytes(int32_t n, int32_t n_cams, const int32_t *widths, const int32_t *heights,
                                 int32_t group, uint64_t pair_capacity);
 
-/* Binds a caller-owned, 256-byte aligned device workspace to *batch and
- * writes the render's per-camera table into it (synchronises the stream
- * once).  Errors: INVALID_ARG for sizes outside the limits above. */
+/* Binds a caller-owned, 256-byte aligned device workspace to *batch, writes
+ * the render's per-camera table into it (synchronises the stream once) and
+ * creates the batch's side streams: inside qb_render_batch the cameras of a
+ * group are binned four at a time on side streams forked from the caller's
+ * stream and joined back to it (captured into a CUDA graph with the rest).
+ * Errors: INVALID_ARG for sizes outside the limits above. */
 qb_status qb_batch_init(qb_batch *batch, int32_t n, int32_t n_cams, const int32_t *widths, const int32_t *heights,
                         int32_t group, uint64_t pair_capacity, void *d_workspace, size_t workspace_bytes,
                         qb_stream_t stream);
+
+/* Destroys the side streams of a batch (after their work is done) and
+ * unbinds its workspace; the caller still owns and frees the workspace. */
+qb_status qb_batch_release(qb_batch *batch);
 
 /* Forward of every camera of the batch (Sec. 2's pipeline with QuadBox
  * binning, Sec. 3, per camera): per group, one preprocess over all (camera,

@@ -118,6 +118,7 @@ _SIGS = [
     ("qb_render_batch_bwd", c_i32, [ctypes.POINTER(QbBatch), ctypes.POINTER(QbScene), ctypes.POINTER(QbCamera),
                                     ctypes.POINTER(c_f), c_vp, ctypes.POINTER(QbSceneGrads), c_vp]),
     ("qb_batch_check", c_i32, [ctypes.POINTER(QbBatch), ctypes.POINTER(c_u64), c_vp]),
+    ("qb_batch_release", c_i32, [ctypes.POINTER(QbBatch)]),
     ("qb_sort_pairs_noalloc_max_scratch", c_size, []),
     ("qb_sort_pairs_noalloc", c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, c_i32, ctypes.POINTER(c_i32), c_vp]),
 ]
@@ -313,6 +314,10 @@ def qb_render_batch_bwd(batch: QbBatch, scene: QbScene, cams_array, bg, dL_dimag
                         stream=None):
     check(load().qb_render_batch_bwd(ctypes.byref(batch), ctypes.byref(scene), cams_array, _bg(bg),
                                      ptr(dL_dimages), ctypes.byref(grads), stream_handle(stream)))
+
+
+def qb_batch_release(batch: QbBatch):
+    check(load().qb_batch_release(ctypes.byref(batch)))
 
 
 def qb_batch_check(batch: QbBatch, stream=None):

@@ -18,6 +18,8 @@
 // workspace for qb_render_batch_bwd, whose render backward is one persistent
 // launch over all cameras' tiles as well.
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "qb_kernels.cuh"
@@ -71,6 +73,12 @@ bool make_geo(int n_cams, const int32_t *W, const int32_t *H, Geo &g) {
     return g.tile_base[n_cams] < (1ull << 32);
 }
 
+// Cameras binned at the same time: each has its own scratch set and side
+// stream (forked from the caller's stream after the group's preprocess and
+// joined before the next one), so one camera's small, latency-bound kernels
+// overlap another's.
+constexpr int kBatchStreams = 4;
+
 struct BLayout {
     size_t xy, shape, conic_o, rgbd, box, r3, meta, counts;  // [n_cams * n] records
     size_t cam_table;                                 // [n_cams] CamTile
@@ -78,8 +86,10 @@ struct BLayout {
     size_t ranges;                                    // [total tiles]
     size_t tfinal, ncontrib, neval;                   // [total pixels]
     size_t segs, dk0, dk1, dv0, dv1;                  // [group * n] group scratch
-    size_t keysA, keysB, valsT;                       // [cap] one camera's pair scratch
+    // one camera's binning scratch, kBatchStreams sets set_stride bytes apart:
+    size_t keysA, keysB, valsT;                       // [cap] pairs
     size_t offsets, counts_e, chunk_first, scan_part, dsort, sort, tile_counts;
+    size_t set_stride;
     size_t gscreen;                                   // [n_cams * n][9]
     size_t queue, state;
     size_t total;
@@ -114,6 +124,7 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
     L.dk1 = take(4 * grecs);
     L.dv0 = take(4 * grecs);
     L.dv1 = take(4 * grecs);
+    const size_t set0 = off;
     L.keysA = take(4 * cap);
     L.keysB = take(4 * cap);
     L.valsT = take(4 * cap);
@@ -131,10 +142,54 @@ bool make_blayout(int n, int n_cams, int group, uint64_t cap, const Geo &g, BLay
     L.dsort = take(db);
     L.sort = take(sb);
     L.tile_counts = take(4 * ((size_t)g.max_tiles + 1));
+    L.set_stride = off - set0;
+    off += (kBatchStreams - 1) * L.set_stride;  // the other sets
     L.gscreen = take(72 * recs);
     L.queue = take(256);
     L.state = take(8 * (size_t)n_cams + 256);
     L.total = off;
+    return true;
+}
+
+// Side streams and events of a batch, keyed by its workspace, created by
+// qb_batch_init and destroyed by qb_batch_release.
+struct SideStreams {
+    int device;
+    cudaStream_t side[kBatchStreams];
+    cudaEvent_t fork, join[kBatchStreams];
+};
+std::mutex g_side_mu;
+std::map<const void *, SideStreams> g_side;
+
+cudaError_t side_create(const void *ws, SideStreams &out) {
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    auto it = g_side.find(ws);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (it != g_side.end() && it->second.device == dev) {
+        out = it->second;
+        return cudaSuccess;
+    }
+    SideStreams ss;
+    std::memset(&ss, 0, sizeof(ss));
+    ss.device = dev;
+    for (int i = 0; i < kBatchStreams && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&ss.side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    g_side[ws] = ss;
+    out = ss;
+    return cudaSuccess;
+}
+
+bool side_find(const void *ws, SideStreams &out) {
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    auto it = g_side.find(ws);
+    if (it == g_side.end()) return false;
+    out = it->second;
     return true;
 }
 
@@ -300,6 +355,33 @@ qb_status qb_batch_init(qb_batch *batch, int32_t n, int32_t n_cams, const int32_
     QB_BCUDA(cudaMemcpyAsync(bat<void>(batch, L.cam_table), table.data(), sizeof(CamTile) * table.size(),
                              cudaMemcpyHostToDevice, s));
     QB_BCUDA(cudaStreamSynchronize(s));  // the host table goes out of scope
+    SideStreams ss;
+    QB_BCUDA(side_create(d_workspace, ss));
+    return QB_OK;
+}
+
+qb_status qb_batch_release(qb_batch *batch) {
+    if (!batch || !batch->workspace) return bfail(QB_ERR_INVALID_ARG, "batch is NULL or not initialised");
+    SideStreams ss;
+    bool found;
+    {
+        std::lock_guard<std::mutex> lock(g_side_mu);
+        auto it = g_side.find(batch->workspace);
+        found = it != g_side.end();
+        if (found) {
+            ss = it->second;
+            g_side.erase(it);
+        }
+    }
+    if (found) {
+        for (int i = 0; i < kBatchStreams; ++i) {
+            QB_BCUDA(cudaStreamSynchronize(ss.side[i]));
+            QB_BCUDA(cudaStreamDestroy(ss.side[i]));
+            QB_BCUDA(cudaEventDestroy(ss.join[i]));
+        }
+        QB_BCUDA(cudaEventDestroy(ss.fork));
+    }
+    batch->workspace = nullptr;
     return QB_OK;
 }
 
@@ -324,9 +406,8 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
     const int rb = t.sort_digit_bits;
     uint64_t *npairs = bat<uint64_t>(b, L.state);
     uint32_t *err = err_word(b, L);
-    uint32_t *keysA = bat<uint32_t>(b, L.keysA), *keysB = bat<uint32_t>(b, L.keysB);
-    uint32_t *valsT = bat<uint32_t>(b, L.valsT);
-    void *sort_scratch = bat<void>(b, L.sort);
+    SideStreams ss;
+    const bool forked = side_find(b->workspace, ss);
     for (int gi = 0; gi < b->n_groups; ++gi) {
         GroupView v;
         group_view(b, geo, cams, gi, v);
@@ -357,19 +438,32 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
         a.depth_keys = bat<uint32_t>(b, L.dk0);  // the depth-order sort's keys and record indices
         a.depth_vals = bat<uint32_t>(b, L.dv0);
         QB_BCUDA(launch_preprocess(a, scene->sh_degree, s));
-        // ---- each camera binned like a frame, into its own slot ----
+        // ---- each camera binned like a frame, into its own slot; camera c on
+        // side stream c % kBatchStreams with that stream's scratch set ----
+        const int nside = forked ? (v.ncam < kBatchStreams ? v.ncam : kBatchStreams) : 0;
+        if (nside > 0) {
+            QB_BCUDA(cudaEventRecord(ss.fork, s));
+            for (int i = 0; i < nside; ++i) QB_BCUDA(cudaStreamWaitEvent(ss.side[i], ss.fork, 0));
+        }
         for (int c = 0; c < v.ncam; ++c) {
             const int k = v.k0 + c;
+            const int set = nside > 0 ? c % nside : 0;
+            const cudaStream_t cs = nside > 0 ? ss.side[set] : s;
+            const size_t so = (size_t)set * L.set_stride;
+            uint32_t *keysA = bat<uint32_t>(b, L.keysA + so), *keysB = bat<uint32_t>(b, L.keysB + so);
+            uint32_t *valsT = bat<uint32_t>(b, L.valsT + so);
+            void *sort_scratch = bat<void>(b, L.sort + so);
             const size_t r0 = (size_t)c * n;  // the camera's records within the group
             uint32_t *dk0 = bat<uint32_t>(b, L.dk0) + r0, *dk1 = bat<uint32_t>(b, L.dk1) + r0;
             uint32_t *dv0 = bat<uint32_t>(b, L.dv0) + r0, *dv1 = bat<uint32_t>(b, L.dv1) + r0;
             int passes = 0;
             if (n > 0)
                 QB_BCUDA(sort_pairs(dk0, dv0, dk1, dv1, (uint64_t)n, nullptr, kDepthBits, kDepthDigitBits,
-                                    bat<void>(b, L.dsort), err, s, &passes));
+                                    bat<void>(b, L.dsort + so), err, cs, &passes));
             const uint32_t *perm = (passes & 1) ? dv1 : dv0;  // group record indices in depth order
-            QB_BCUDA(launch_scan(a.counts, perm, n, bat<uint32_t>(b, L.offsets), bat<uint64_t>(b, L.scan_part),
-                                 npairs + k, err, s, bat<uint32_t>(b, L.counts_e), bat<uint32_t>(b, L.chunk_first),
+            QB_BCUDA(launch_scan(a.counts, perm, n, bat<uint32_t>(b, L.offsets + so),
+                                 bat<uint64_t>(b, L.scan_part + so), npairs + k, err, cs,
+                                 bat<uint32_t>(b, L.counts_e + so), bat<uint32_t>(b, L.chunk_first + so),
                                  (uint32_t)chunk_table_size(cap)));
             const int ntiles = geo.tx[k] * geo.ty[k];
             const int tile_bits = bits_for((uint64_t)ntiles);
@@ -388,9 +482,9 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
             e.meta = a.meta;
             e.rgbd = a.rgbd;
             e.counts = a.counts;
-            e.offsets = bat<uint32_t>(b, L.offsets);
-            e.counts_e = bat<uint32_t>(b, L.counts_e);
-            e.chunk_first = bat<uint32_t>(b, L.chunk_first);
+            e.offsets = bat<uint32_t>(b, L.offsets + so);
+            e.counts_e = bat<uint32_t>(b, L.counts_e + so);
+            e.chunk_first = bat<uint32_t>(b, L.chunk_first + so);
             e.segs = bat<uint4>(b, L.segs);
             e.vals = into_a ? slot : valsT;
             e.n_pairs = npairs + k;
@@ -400,16 +494,20 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
             e.clamp3s = a.clamp3s;
             e.err = err;
             e.ts = v.ts;
-            QB_BCUDA(launch_emit<uint32_t>(e, into_a ? keysA : keysB, s));
+            QB_BCUDA(launch_emit<uint32_t>(e, into_a ? keysA : keysB, cs));
             // per-tile counts -> the camera's ranges and every pass's bucket
             // offsets; then the tile sort, whose last pass writes the slot
             uint2 *ranges = bat<uint2>(b, L.ranges) + geo.tile_base[k];
             QB_BCUDA(launch_tile_count(into_a ? keysA : keysB, cap, npairs + k, ntiles,
-                                       bat<uint32_t>(b, L.tile_counts), ranges, sort_hist_table(sort_scratch),
-                                       sort_hist_stride(), rb, tile_bits, s));
+                                       bat<uint32_t>(b, L.tile_counts + so), ranges, sort_hist_table(sort_scratch),
+                                       sort_hist_stride(), rb, tile_bits, cs));
             if (tpasses > 0)
                 QB_BCUDA(tile_sort_passes(keysA, slot, keysB, valsT, cap, cap, npairs + k, tile_bits, 0, rb,
-                                          sort_scratch, err, s));
+                                          sort_scratch, err, cs));
+        }
+        for (int i = 0; i < nside; ++i) {  // join before the next group's preprocess reuses the group scratch
+            QB_BCUDA(cudaEventRecord(ss.join[i], ss.side[i]));
+            QB_BCUDA(cudaStreamWaitEvent(s, ss.join[i], 0));
         }
     }
     // ---- one persistent render over every camera's tiles ----

@@ -277,6 +277,14 @@ class Batch:
         N.qb_batch_init(self.batch, self.n, self.widths, self.heights, self.group, self.pair_capacity, self.ws, stream)
         self.images = torch.empty(int(self.batch.total_floats), dtype=torch.float32, device=device)
 
+    def __del__(self):
+        # the library's side streams of this batch (the workspace is torch's)
+        try:
+            if self.batch.workspace:
+                N.qb_batch_release(self.batch)
+        except Exception:
+            pass
+
     @property
     def n_cams(self):
         return len(self.widths)
