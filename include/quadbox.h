@@ -176,7 +176,8 @@ typedef struct {
     float *t_final;     /* [H][W]  transmittance after the last contributor */
     int32_t *n_contrib; /* [H][W]  1 + position of the last contributor     */
     int32_t *n_eval;    /* [H][W]  list entries the pixel evaluated before it
-                                   stopped (render statistics)               */
+                                   stopped (render statistics; written by
+                                   qb_render_fwd_counted only)               */
     uint64_t *n_pairs;  /* [1]     P on the device                          */
     uint32_t *err_flags;/* [2]     [0]: bit0 capacity, bit1 timeout.  [1]:
                                    test-only, zero after qb_frame_init; a test

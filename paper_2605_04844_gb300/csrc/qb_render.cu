@@ -44,8 +44,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // The compositing state of one packed pair of pixels.
 struct RenderPair {
     float2 T, cr, cg, cb, npy;
-    bool in0, in1, done0, done1;
-    int n0, n1, last0, last1;
+    bool done0, done1;
+    int n0, n1, last0, last1;  // n0, n1: the counted variant only
 };
 
 // Both pixels of a pair are composited in lock step: every entry's exponent
@@ -70,13 +70,12 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
 #pragma unroll
     for (int r = 0; r < kRenderPairs; ++r) {
         const int y0 = pyb + 4 * r, y1 = y0 + 2;
-        P[r].in0 = px < C.W && y0 < C.H;
-        P[r].in1 = px < C.W && y1 < C.H;
-        P[r].done0 = !P[r].in0;
-        P[r].done1 = !P[r].in1;
+        const bool in0 = px < C.W && y0 < C.H, in1 = px < C.W && y1 < C.H;
+        P[r].done0 = !in0;
+        P[r].done1 = !in1;
         // a pixel outside the image (later: one that has stopped) carries a
         // NaN row, so its exponent is NaN and fails every test
-        P[r].npy = f2(P[r].in0 ? -(float)y0 : kNaN, P[r].in1 ? -(float)y1 : kNaN);
+        P[r].npy = f2(in0 ? -(float)y0 : kNaN, in1 ? -(float)y1 : kNaN);
         P[r].T = f2(1.f, 1.f);
         P[r].cr = P[r].cg = P[r].cb = f2(0.f, 0.f);
         P[r].n0 = P[r].n1 = P[r].last0 = P[r].last1 = 0;
@@ -172,8 +171,10 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
                 const bool st0 = ok0 && tT.x < kTStop, st1 = ok1 && tT.y < kTStop;
                 const bool ac0 = ok0 && !st0, ac1 = ok1 && !st1;
                 if (st0 || st1) {  // once in a pixel's life: record the stop, poison its row
-                    if (st0) q.n0 = nj, q.done0 = true, q.npy.x = kNaN;
-                    if (st1) q.n1 = nj, q.done1 = true, q.npy.y = kNaN;
+                    if (st0) q.done0 = true, q.npy.x = kNaN;
+                    if (st1) q.done1 = true, q.npy.y = kNaN;
+                    if (COUNT && st0) q.n0 = nj;
+                    if (COUNT && st1) q.n1 = nj;
                 }
                 // alpha of the accepted entries, 0 elsewhere: T (1 - 0) = T and
                 // c + r * 0 = c exactly, so the updates need no select
@@ -195,13 +196,12 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
     for (int r = 0; r < kRenderPairs; ++r) {
         RenderPair &q = P[r];
         // a pixel that never stopped evaluated the whole list
-        if (!q.done0) q.n0 = total;
-        if (!q.done1) q.n1 = total;
+        if (COUNT && !q.done0) q.n0 = total;
+        if (COUNT && !q.done1) q.n1 = total;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const bool in = h ? q.in1 : q.in0;
-            if (!in) continue;
             const int py = pyb + 4 * r + 2 * h;
+            if (px >= C.W || py >= C.H) continue;
             const size_t pix = (size_t)py * C.W + px;
             const float T = h ? q.T.y : q.T.x;
             img[pix] = fmaf(T, a.bg[0], h ? q.cr.y : q.cr.x);
@@ -209,8 +209,10 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
             img[2 * plane + pix] = fmaf(T, a.bg[2], h ? q.cb.y : q.cb.x);
             a.tfinal[C.pix_base + pix] = T;
             a.ncontrib[C.pix_base + pix] = h ? q.last1 : q.last0;
-            a.neval[C.pix_base + pix] = h ? q.n1 : q.n0;
-            ev += (unsigned long long)(h ? q.n1 : q.n0);
+            if (COUNT) {
+                a.neval[C.pix_base + pix] = h ? q.n1 : q.n0;
+                ev += (unsigned long long)(h ? q.n1 : q.n0);
+            }
         }
     }
     if (COUNT) {
