@@ -132,6 +132,35 @@ constexpr float kElongatedF2 = 0.01f;  // f < 0.1: aspect ratio above 10 : 1
 // them first never changes a decision of that test.
 __device__ __forceinline__ float skip_threshold(float o) { return -logf(255.0f * o) - 1e-3f; }
 
+// Whether some point of the pixel rectangle [x0, x1] x [y0, y1] can give the
+// Gaussian (mu^2D, conic (a, b, c)) an exponent above t, i.e. whether the
+// rectangle meets the ellipse q(d) = a dx^2 + 2 b dx dy + c dy^2 <= -2t,
+// d = mu^2D - pixel.  q is convex, so its minimum over the rectangle is 0 when
+// mu^2D lies inside and otherwise lies on an edge, where it is the 1D
+// minimiser clamped to the edge.  The test is conservative: the radius gets a
+// 1 % + 0.01 margin, far above the float32 error of q and of the kernels'
+// exponents for conics whose stretching factor is above kElongatedF2, and an
+// elongated or degenerate conic always meets the rectangle.
+__device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, float b, float c, float t,
+                                                   bool elongated, float x0, float y0, float x1, float y1) {
+    if (elongated || !(a > 0.f && c > 0.f)) return true;
+    const float r2 = fmaxf(-2.f * t, 0.f) * 1.01f + 1e-2f;
+    const float ul = mx - x1, uh = mx - x0, vl = my - y1, vh = my - y0;
+    if (ul <= 0.f && uh >= 0.f && vl <= 0.f && vh >= 0.f) return true;
+    const float ia = 1.f / a, ic = 1.f / c;
+    float best = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float v = e ? vh : vl;  // horizontal edge: dy fixed
+        const float u = fminf(fmaxf(-b * v * ia, ul), uh);
+        best = fminf(best, fmaf(a * u, u, fmaf(2.f * b * u, v, c * v * v)));
+        const float u2 = e ? uh : ul;  // vertical edge: dx fixed
+        const float v2 = fminf(fmaxf(-b * u2 * ic, vl), vh);
+        best = fminf(best, fmaf(a * u2, u2, fmaf(2.f * b * u2, v2, c * v2 * v2)));
+    }
+    return best <= r2;
+}
+
 // Exponent of the 2D Gaussian at offset (dx, dy) = mu^2D - pixel,
 // -(a dx^2 + 2 b dx dy + c dy^2) / 2, evaluated as a quadratic in dy:
 //   A + dy (B + cc dy),  A = ca dx^2, B = cb dx,
