@@ -512,7 +512,7 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream) {
             QB_CUDA(tile_sort_passes(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
                                      at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1), frame->pair_capacity,
                                      n_max, n_dev, tile_bits, frame->reserved[2], rb, at<void>(frame, L.sort_scratch),
-                                     err, s));
+                                     err, s, (uint64_t)frame->n));
         frame->sorted_in_alt = 0;  // the values end in vals0; the tile of each is given by the ranges
         (void)ntiles;
     } else {

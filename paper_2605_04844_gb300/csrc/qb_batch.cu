@@ -503,7 +503,7 @@ qb_status qb_render_batch(qb_batch *b, const qb_scene *scene, const qb_camera *c
                                        sort_hist_stride(), rb, tile_bits, cs));
             if (tpasses > 0)
                 QB_BCUDA(tile_sort_passes(keysA, slot, keysB, valsT, cap, cap, npairs + k, tile_bits, 0, rb,
-                                          sort_scratch, err, cs));
+                                          sort_scratch, err, cs, (uint64_t)b->group * (uint64_t)b->n));
         }
         for (int i = 0; i < nside; ++i) {  // join before the next group's preprocess reuses the group scratch
             QB_BCUDA(cudaEventRecord(ss.join[i], ss.side[i]));

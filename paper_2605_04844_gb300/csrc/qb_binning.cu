@@ -469,8 +469,9 @@ __global__ void __launch_bounds__(kSortBlock) emit_sweep_kernel(EmitArgs a, uint
         val[k] = valid ? wv[q] : 0u;
     }
     __syncthreads();  // the pass body reuses the staging memory
-    sweep_tile<RB, uint32_t, WRITE_KEYS>(key, [&](int k) { return val[k]; }, (uint32_t)P, (uint32_t)tbase, tile,
-                                         bin_off, lookback, 0, mask, a.err, kout, vout, smem);
+    sweep_tile<RB, uint32_t, WRITE_KEYS ? kOutPairs : kOutValues>(key, [&](int k) { return val[k]; }, (uint32_t)P,
+                                                                  (uint32_t)tbase, tile, bin_off, lookback, 0, mask,
+                                                                  a.err, kout, vout, smem);
 }
 
 template <int RB, bool WRITE_KEYS>

@@ -113,9 +113,12 @@ cudaError_t sort_clear(void *scratch, uint64_t n_cap, int digit_bits, int first_
 // Passes [first_pass, passes) of the tile sort on bits [0, end_bit) (pass
 // widths from pass_geo): pass p writes buffer A when passes - 1 - p is even,
 // else B, reading the other; the last pass writes values only (into A).
+// Values are below val_bound; a two-pass sort from pass 0 whose values fit
+// beside the second digit in one word carries packed words between its
+// passes and leaves vB unused.
 cudaError_t tile_sort_passes(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, uint64_t n_cap, uint64_t n_max,
                              const uint64_t *n_dev, int end_bit, int first_pass, int digit_bits, void *scratch,
-                             uint32_t *err, cudaStream_t s);
+                             uint32_t *err, cudaStream_t s, uint64_t val_bound);
 inline bool pass_writes_a(int passes, int p) { return ((passes - 1 - p) & 1) == 0; }
 
 // ---- device helpers -----------------------------------------------------------

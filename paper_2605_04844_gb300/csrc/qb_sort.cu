@@ -127,15 +127,17 @@ __global__ void __launch_bounds__(1024) sort_hist_scan_kernel(uint32_t *hist, Pa
     }
 }
 
-// One digit pass over pairs already in memory.
-template <int RB, typename KeyT, bool WRITE_KEYS>
+// One digit pass over pairs already in memory.  OUT: what it writes
+// (SweepOut).  PACKED_IN: kin holds packed words (key bits above vbits, the
+// value below) and vin is not read.
+template <int RB, typename KeyT, int OUT, bool PACKED_IN>
 __global__ void __launch_bounds__(kSortBlock, sizeof(KeyT) == 4 ? kSortBlocksPerSM : 3) onesweep_kernel(const KeyT *__restrict__ kin,
                                                               const uint32_t *__restrict__ vin,
                                                               KeyT *__restrict__ kout, uint32_t *__restrict__ vout,
                                                               uint64_t n_max, const uint64_t *n_dev,
                                                               const uint32_t *__restrict__ bin_off,
                                                               uint32_t *lookback, uint32_t *counter, int shift,
-                                                              uint32_t mask, uint32_t *err) {
+                                                              uint32_t mask, uint32_t *err, int pack_shift, int vbits) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -155,37 +157,48 @@ __global__ void __launch_bounds__(kSortBlock, sizeof(KeyT) == 4 ? kSortBlocksPer
         const uint32_t idx = wbase + 32 * k + lane;
         key[k] = idx < n ? __ldcs(kin + idx) : KeyT(0);
     }
-    auto val = [&](int k) -> uint32_t { return __ldcs(vin + wbase + 32 * k + lane); };
-    sweep_tile<RB, KeyT, WRITE_KEYS>(key, val, n, tbase, tile, bin_off, lookback, shift, mask, err, kout, vout,
-                                     smem);
+    if constexpr (PACKED_IN) {
+        const uint32_t vmask = (1u << vbits) - 1u;
+        auto val = [&](int k) -> uint32_t { return (uint32_t)key[k] & vmask; };
+        sweep_tile<RB, KeyT, OUT>(key, val, n, tbase, tile, bin_off, lookback, shift, mask, err, kout, vout, smem,
+                                  pack_shift, vbits);
+    } else {
+        auto val = [&](int k) -> uint32_t { return __ldcs(vin + wbase + 32 * k + lane); };
+        sweep_tile<RB, KeyT, OUT>(key, val, n, tbase, tile, bin_off, lookback, shift, mask, err, kout, vout, smem,
+                                  pack_shift, vbits);
+    }
 }
 
-template <int RB, typename KeyT, bool WRITE_KEYS>
+template <int RB, typename KeyT, int OUT, bool PACKED_IN>
 static cudaError_t launch_pass_t(const KeyT *kin, const uint32_t *vin, KeyT *kout, uint32_t *vout, uint64_t n_max,
                                  const uint64_t *n_dev, const uint32_t *bin_off, uint32_t *lookback,
-                                 uint32_t *counter, int shift, uint32_t mask, uint32_t *err, const char *name,
-                                 cudaStream_t s) {
+                                 uint32_t *counter, int shift, uint32_t mask, uint32_t *err, int pack_shift, int vbits,
+                                 const char *name, cudaStream_t s) {
     constexpr size_t smem = sweep_smem<RB, KeyT>();
-    cudaError_t e = ensure_dyn_smem((const void *)onesweep_kernel<RB, KeyT, WRITE_KEYS>, smem);
+    cudaError_t e = ensure_dyn_smem((const void *)onesweep_kernel<RB, KeyT, OUT, PACKED_IN>, smem);
     if (e != cudaSuccess) return e;
-    note_launch(name, s), onesweep_kernel<RB, KeyT, WRITE_KEYS><<<(unsigned)sort_tiles(n_max), kSortBlock, smem, s>>>(
-        kin, vin, kout, vout, n_max, n_dev, bin_off, lookback, counter, shift, mask, err);
+    note_launch(name, s),
+        onesweep_kernel<RB, KeyT, OUT, PACKED_IN><<<(unsigned)sort_tiles(n_max), kSortBlock, smem, s>>>(
+            kin, vin, kout, vout, n_max, n_dev, bin_off, lookback, counter, shift, mask, err, pack_shift, vbits);
     return cudaGetLastError();
 }
 
-// One pass on the digit bits [shift, shift + bits), bits <= 11.
+// One pass on the digit bits [shift, shift + bits), bits <= 11, writing keys
+// and values (write_keys) or values only.
 template <typename KeyT>
 static cudaError_t launch_pass(const KeyT *kin, const uint32_t *vin, KeyT *kout, uint32_t *vout, uint64_t n_max,
                                const uint64_t *n_dev, const uint32_t *bin_off, uint32_t *lookback,
                                uint32_t *counter, int shift, int bits, uint32_t *err, bool write_keys,
                                const char *name, cudaStream_t s) {
     const uint32_t mask = (1u << bits) - 1u;
-#define QB_PASS_CASE(RB)                                                                                          \
-    case RB:                                                                                                      \
-        return write_keys ? launch_pass_t<RB, KeyT, true>(kin, vin, kout, vout, n_max, n_dev, bin_off, lookback,  \
-                                                          counter, shift, mask, err, name, s)                     \
-                          : launch_pass_t<RB, KeyT, false>(kin, vin, kout, vout, n_max, n_dev, bin_off, lookback, \
-                                                           counter, shift, mask, err, name, s);
+#define QB_PASS_CASE(RB)                                                                                           \
+    case RB:                                                                                                       \
+        return write_keys ? launch_pass_t<RB, KeyT, kOutPairs, false>(kin, vin, kout, vout, n_max, n_dev, bin_off, \
+                                                                      lookback, counter, shift, mask, err, 0, 0,   \
+                                                                      name, s)                                     \
+                          : launch_pass_t<RB, KeyT, kOutValues, false>(kin, vin, kout, vout, n_max, n_dev,        \
+                                                                       bin_off, lookback, counter, shift, mask,    \
+                                                                       err, 0, 0, name, s);
     switch (bits < 4 ? 4 : bits) {
         QB_PASS_CASE(4)
         QB_PASS_CASE(5)
@@ -250,16 +263,54 @@ cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint3
                      hist_ready);
 }
 
+// The two passes of a tile sort whose values fit beside the second digit in
+// one word: the first pass writes (key >> shift1) << vbits | value, one 4-byte
+// word instead of a key and a value, and the second reads that word alone
+// (digit above vbits, value below), 20 bytes of traffic per pair over the two
+// passes instead of 28.
+template <int RB0, int RB1>
+static cudaError_t packed_passes(const uint32_t *kA, const uint32_t *vA, uint32_t *kB, uint32_t *vOut,
+                                 uint64_t n_cap, uint64_t n_max, const uint64_t *n_dev, const PassGeo &g,
+                                 int digit_bits, void *scratch, uint32_t *err, cudaStream_t s) {
+    const uint32_t *hist = sort_hist_table(scratch);
+    const int vbits = 32 - RB1;
+    cudaError_t e = launch_pass_t<RB0, uint32_t, kOutPacked, false>(
+        kA, vA, kB, nullptr, n_max, n_dev, hist, sort_lookback(scratch, n_cap, digit_bits, 0), sort_counter(scratch, 0),
+        g.shift[0], (1u << RB0) - 1u, err, g.shift[1], vbits, "tile_sort_pass", s);
+    if (e != cudaSuccess) return e;
+    return launch_pass_t<RB1, uint32_t, kOutValues, true>(
+        kB, nullptr, nullptr, vOut, n_max, n_dev, hist + kHistStride, sort_lookback(scratch, n_cap, digit_bits, 1),
+        sort_counter(scratch, 1), vbits, (1u << RB1) - 1u, err, 0, vbits, "tile_sort_pass_values", s);
+}
+
 // Passes [first_pass, passes) of the depth-first tile sort on bits
 // [0, end_bit) (bucket offsets already in the table).  Pass p writes buffer A
 // when passes - 1 - p is even, else B, and reads the other one; the last pass
-// writes values only, into A.
+// writes values only, into A.  Every value is below val_bound: a sort of two
+// passes from the first whose values fit in 32 - (second digit's bits) bits
+// takes the packed form (packed_passes; B's value buffer is then not used).
 cudaError_t tile_sort_passes(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, uint64_t n_cap, uint64_t n_max,
                              const uint64_t *n_dev, int end_bit, int first_pass, int digit_bits, void *scratch,
-                             uint32_t *err, cudaStream_t s) {
+                             uint32_t *err, cudaStream_t s, uint64_t val_bound) {
     const PassGeo g = pass_geo(end_bit, digit_bits);
     cudaError_t e = sort_clear(scratch, n_cap, digit_bits, first_pass, g.passes, s);
     if (e != cudaSuccess || n_max == 0) return e;
+    if (first_pass == 0 && g.passes == 2 && val_bound <= (1ull << (32 - g.bits[1]))) {
+        // pass 0 reads A and writes B, pass 1 reads B and writes A's values;
+        // tile ids of 9 to 16 bits: first digits of 5 to 8 bits, the second
+        // of the same width or one bit less
+        const int b0 = g.bits[0], b1 = g.bits[1];
+#define QB_PACKED_CASE(B0)                                                                                   \
+    if (b0 == B0 && b1 == B0)                                                                                \
+        return packed_passes<B0, B0>(kA, vA, kB, vA, n_cap, n_max, n_dev, g, digit_bits, scratch, err, s);  \
+    if (b0 == B0 && b1 == B0 - 1)                                                                            \
+        return packed_passes<B0, B0 - 1>(kA, vA, kB, vA, n_cap, n_max, n_dev, g, digit_bits, scratch, err, s);
+        QB_PACKED_CASE(5)
+        QB_PACKED_CASE(6)
+        QB_PACKED_CASE(7)
+        QB_PACKED_CASE(8)
+#undef QB_PACKED_CASE
+    }
     const uint32_t *hist = sort_hist_table(scratch);
     for (int p = first_pass; p < g.passes; ++p) {
         const bool to_a = pass_writes_a(g.passes, p);

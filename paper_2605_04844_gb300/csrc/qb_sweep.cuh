@@ -106,19 +106,29 @@ constexpr size_t sweep_smem() {
     return (size_t)kSortTile * 8 + (size_t)kSortWarps * (1 << RB) * 2 + (size_t)3 * (1 << RB) * 4;
 }
 
+// What a pass writes at each output position.
+enum SweepOut : int {
+    kOutPairs = 0,   // the key to kout and the value to vout
+    kOutValues = 1,  // the value only (the last pass, whose keys the per-tile ranges imply)
+    kOutPacked = 2,  // one word to kout: (key >> pack_shift) << vbits | value
+};
+
 // One pass over the tile `tile` (positions [tbase, tbase + kSortTile) of n) on the
 // digit (key >> shift) & mask, mask < 2^RB.  val(k) gives item k's value; it
 // is asked for only at the scatter, after the ranking (so a caller can load
 // values late and keep fewer registers live).  bin_off: the pass's exclusive
-// bucket offsets; lookback: the pass's status words [tiles][2^RB].  With
-// WRITE_KEYS false only the values are written (the last pass, whose keys are
-// implied by the per-tile ranges).
-template <int RB, typename KeyT, bool WRITE_KEYS, class ValFn>
+// bucket offsets; lookback: the pass's status words [tiles][2^RB].  OUT
+// (SweepOut) says what is written; kOutPacked (32-bit keys) needs values
+// below 2^vbits and keys below 2^(pack_shift + 32 - vbits).
+template <int RB, typename KeyT, int OUT, class ValFn>
 __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn &&val,
                                            uint32_t n, uint32_t tbase, uint32_t tile,
                                            const uint32_t *__restrict__ bin_off, uint32_t *lookback, int shift,
                                            uint32_t mask, uint32_t *err, KeyT *__restrict__ kout,
-                                           uint32_t *__restrict__ vout, uint8_t *smem) {
+                                           uint32_t *__restrict__ vout, uint8_t *smem, int pack_shift = 0,
+                                           int vbits = 0) {
+    static_assert(OUT != kOutPacked || sizeof(KeyT) == 4, "packed output is for 32-bit keys");
+    constexpr bool WRITE_KEYS = OUT != kOutValues;
     constexpr int R = 1 << RB;
     constexpr int PER = (R + kSortBlock - 1) / kSortBlock;
     uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem + (size_t)kSortTile * 8);
@@ -288,8 +298,12 @@ __device__ __forceinline__ void sweep_tile(const KeyT (&key)[kSortItems], ValFn 
                 const uint32_t d = (kv.x >> shift) & mask;
                 const uint32_t dest = s_gbase[d] + j;
                 if (dest < n) {  // dest >= n only after a look-back timeout
-                    if (WRITE_KEYS) kout[dest] = (KeyT)kv.x;
-                    vout[dest] = kv.y;
+                    if (OUT == kOutPacked) {
+                        kout[dest] = (KeyT)(((kv.x >> pack_shift) << vbits) | kv.y);
+                    } else {
+                        if (WRITE_KEYS) kout[dest] = (KeyT)kv.x;
+                        vout[dest] = kv.y;
+                    }
                 }
             }
         }
