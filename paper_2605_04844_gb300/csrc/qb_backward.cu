@@ -220,8 +220,10 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
             bool e[4];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                e[2 * r] = p < P[r].last0 && pw[r].x <= 0.f && pw[r].x >= K.z;
-                e[2 * r + 1] = p < P[r].last1 && pw[r].y <= 0.f && pw[r].y >= K.z;
+                // the forward's test: power >= skip (a positive power is a
+                // rounding of 0, kept)
+                e[2 * r] = p < P[r].last0 && pw[r].x >= K.z;
+                e[2 * r + 1] = p < P[r].last1 && pw[r].y >= K.z;
             }
             if (!__any_sync(0xffffffffu, e[0] || e[1] || e[2] || e[3])) continue;
             const float4 C1 = S.s3[j], C2 = S.s4[j];

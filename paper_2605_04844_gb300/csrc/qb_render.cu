@@ -9,8 +9,9 @@
 // depth-sorted Gaussian list is walked in
 // batches staged in shared memory (mu^2D, the skip threshold, opacity, the
 // rescaled conic and the colour).  Per entry and pixel (3DGS conventions):
-//   power = -(a dx^2 + 2 b dx dy + c dy^2)/2, skip if power > 0 or if it is
-//   so low that alpha is certainly below 1/255;
+//   power = -(a dx^2 + 2 b dx dy + c dy^2)/2, skip if it is so low that alpha
+//   is certainly below 1/255 (power > 0 arises only as a float32 rounding of
+//   0 and is kept);
 //   alpha = min(0.99, o e^power), skip if alpha < 1/255;
 //   T' = T (1 - alpha); stop before adding once T' < 1e-4;
 //   C += alpha T c; T = T'.
@@ -166,16 +167,15 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
                     }
                 }
                 const float op = fabsf(K.w);
-                const float2 nsk = f2(-K.z, -K.z);
                 bool e0[kRenderPairs], e1[kRenderPairs];
                 bool any = false;
 #pragma unroll
                 for (int r = 0; r < kRenderPairs; ++r) {
-                    // skip < power <= 0 as one sign test: power (power - skip) <= 0
-                    // (skip < 0; the signs of a difference and a product are exact)
-                    const float2 t = __fmul2_rn(pw[r], __fadd2_rn(pw[r], nsk));
-                    e0[r] = t.x <= 0.f;
-                    e1[r] = t.y <= 0.f;
+                    // power >= skip; the rule power <= 0 needs no test: a
+                    // positive exponent is a float32 rounding of 0 (the conic is
+                    // positive definite), where alpha = o e^power rounds like o
+                    e0[r] = pw[r].x >= K.z;
+                    e1[r] = pw[r].y >= K.z;
                     if (COUNT) npass += (uint32_t)e0[r] + (uint32_t)e1[r];
                     any = any || e0[r] || e1[r];
                 }
