@@ -444,10 +444,23 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
-def kernel_work(P, n, evals):
+def tile_sort_packed(n, W, H, digit_bits):
+    """Whether the library's two-pass tile sort of this frame carries packed
+    words between its passes: two passes whose first digit has 5 to 8 bits,
+    and Gaussian indices below 2^(32 - second digit's bits)."""
+    tiles = -(-W // 16) * -(-H // 16)
+    tile_bits = max(1, (tiles - 1).bit_length())
+    if -(-tile_bits // digit_bits) != 2:
+        return False
+    b0, b1 = -(-tile_bits // 2), tile_bits // 2
+    return 5 <= b0 <= 8 and n <= 2 ** (32 - b1)
+
+
+def kernel_work(P, n, evals, packed=False):
     """Algorithmic work per launch of each forward kernel at this frame: HBM
     bytes (what the kernel must move at least) or FP32 operations.  evals:
-    (pixel-entry evaluations, those whose power test passed) of the render."""
+    (pixel-entry evaluations, those whose power test passed) of the render.
+    packed: the tile sort's passes exchange one packed word per pair."""
     n_eval, n_pass = evals if evals else (0, 0)
     return {
         "preprocess_kernel": ("hbm", n * PREPROCESS_BYTES),
@@ -456,8 +469,10 @@ def kernel_work(P, n, evals):
         "scan_onepass_kernel": ("hbm", n * 12),        # depth order read, counts gathered, offsets written
         "emit_warp_kernel": ("hbm", P * 8 + n * 28),     # pairs written; depth order, offset, count, segments
         "tile_count_kernel": ("hbm", P * 4),             # the tile ids once
-        "tile_sort_pass": ("hbm", P * 16),               # key + value read and written
-        "tile_sort_pass_values": ("hbm", P * 12),        # key + value read, value written
+        # key + value read, and written (packed: one word written)
+        "tile_sort_pass": ("hbm", P * (12 if packed else 16)),
+        # key + value (packed: one word) read, value written
+        "tile_sort_pass_values": ("hbm", P * (8 if packed else 12)),
         "render_kernel": ("alu", n_eval * RENDER_FLOPS_POWER_TEST + n_pass * RENDER_FLOPS_PASSED),
     }
 
@@ -489,7 +504,7 @@ def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, evals, clk, sort_mode,
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    work = kernel_work(P, n, evals)
+    work = kernel_work(P, n, evals, packed=sort_mode != "full_key" and tile_sort_packed(n, W, H, digit_bits))
     n_eval = evals[0] if evals else 0
     rows = {}
     for name, k in kernels.items():

@@ -87,6 +87,8 @@ bool make_layout(int n, int W, int H, uint64_t cap, Layout &L) {
     L.tile_counts = take(4 * ((size_t)tiles + 1));  // + the tile histogram's block counter
     L.tile_diff = take(4 * (size_t)(tx + 1) * (ty + 1));
     L.tile_single = take(4 * (size_t)tiles);
+    L.order_cnt = take(4 * 2 * (size_t)kOrderBuckets);
+    L.order_list = take(4 * 2 * (size_t)kOrderBuckets * tiles);
     L.tfinal = take(4 * (size_t)W * H);
     L.ncontrib = take(4 * (size_t)W * H);
     L.neval = take(4 * (size_t)W * H);
@@ -399,7 +401,6 @@ qb_status qb_bin_emit(qb_frame *frame, uint64_t *n_pairs_out, qb_stream_t stream
     if (eff == QB_SORT_DEPTH_FIRST && fused) {
         // per-tile counts -> ranges and the tile sort's bucket offsets
         const int tile_bits = frame->key_bits - kDepthBits;
-        const int passes = tile_bits > 0 ? (tile_bits + frame->sort_digit_bits - 1) / frame->sort_digit_bits : 0;
         const uint32_t zero_off[1] = {0u};
         QB_CUDA(launch_tile_prep(at<int>(frame, L.tile_diff), at<int>(frame, L.tile_single), frame_tileset(frame),
                                  zero_off, zero_off,
@@ -552,6 +553,15 @@ static qb_status render_fwd_impl(qb_frame *frame, const float *bg, float *d_img,
     a.ncontrib = at<int>(frame, L.ncontrib);
     a.neval = at<int>(frame, L.neval);
     a.counts = counts;
+    // heaviest tiles first: every tile filed by a work estimate, then blocks
+    // take the tiles in that order (the last blocks to start are short ones);
+    // the render files every tile again by the backward's work
+    const size_t ntiles = a.ts.total_tiles;
+    uint32_t *cnt = at<uint32_t>(frame, L.order_cnt), *list = at<uint32_t>(frame, L.order_list);
+    a.order = TileOrder{cnt, list};
+    a.order_out = TileOrder{cnt + kOrderBuckets, list + (size_t)kOrderBuckets * ntiles};
+    QB_CUDA(cudaMemsetAsync(cnt, 0, 4 * 2 * (size_t)kOrderBuckets, (cudaStream_t)stream));
+    QB_CUDA(launch_tile_work(a, (cudaStream_t)stream));
     QB_CUDA(launch_render(a, frame->render_batch, (cudaStream_t)stream));
     frame->stage = 4;
     return QB_OK;
@@ -603,6 +613,10 @@ qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera 
     b.tfinal = at<float>(frame, L.tfinal);
     b.ncontrib = at<int>(frame, L.ncontrib);
     b.g_screen = gscreen;
+    // tiles by decreasing last-contributor count (the backward's work per
+    // tile, filed by the forward render)
+    b.order = TileOrder{at<uint32_t>(frame, L.order_cnt) + kOrderBuckets,
+                        at<uint32_t>(frame, L.order_list) + (size_t)kOrderBuckets * b.ts.total_tiles};
     QB_CUDA(launch_render_bwd(b, s));
     PreBwdArgs p;
     std::memset(&p, 0, sizeof(p));

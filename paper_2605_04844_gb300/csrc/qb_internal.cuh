@@ -48,6 +48,8 @@ struct Layout {
     size_t tile_counts;  // per-tile pair counts of the tile histogram (+ its block counter)
     size_t tile_diff;  // (tiles_y+1) x (tiles_x+1) int difference array
     size_t tile_single;  // tiles ints: pair counts of single-tile Gaussians
+    size_t order_cnt;   // [2][kOrderBuckets]: the render's and the backward's tile orders (TileOrder)
+    size_t order_list;  // [2][kOrderBuckets][tiles]
     size_t gscreen;  // [n][9] screen-space gradients
     size_t state;  // u64 n_pairs, u32 err_flags, padding
     size_t total;

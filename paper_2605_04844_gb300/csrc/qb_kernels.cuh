@@ -109,6 +109,49 @@ struct EmitArgs {
     TileSet ts;  // camera of record r is r / n_per_cam
 };
 
+// Tiles filed by work into kOrderBuckets buckets, heaviest first: bucket
+// j = kOrderBuckets - 1 - min(work / kOrderWidth, kOrderBuckets - 1) holds
+// cnt[j] tiles at list[j * ntiles ...]; position p of the order is slot
+// p - (cnt[0] + ... + cnt[j - 1]) of the bucket j that contains it.  The
+// counts are zeroed before the tiles are filed, each tile exactly once.
+constexpr int kOrderBuckets = 64;
+constexpr uint32_t kOrderWidth = 16;  // entries of work per bucket
+struct TileOrder {
+    uint32_t *cnt;   // [kOrderBuckets], or null: no order
+    uint32_t *list;  // [kOrderBuckets][ntiles]
+};
+
+__device__ __forceinline__ void order_file(const TileOrder &o, uint32_t ntiles, uint32_t tile, uint32_t work) {
+    const uint32_t j = (uint32_t)kOrderBuckets - 1u - min(work / kOrderWidth, (uint32_t)kOrderBuckets - 1u);
+    const uint32_t slot = atomicAdd(o.cnt + j, 1u);
+    if (slot < ntiles) o.list[(size_t)j * ntiles + slot] = tile;
+}
+
+// The tile at position pos of the order, for a block of kOrderBuckets threads
+// (thread j reads bucket j); s: three words of shared memory.  Position pos
+// itself when no bucket holds it (never, when every tile was filed once).
+__device__ __forceinline__ uint32_t order_pick(const TileOrder &o, uint32_t ntiles, uint32_t pos, uint32_t *s) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t c = o.cnt[tid];
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += u;
+    }
+    if (tid == 31) s[0] = incl;
+    if (tid == 0) s[1] = pos;
+    __syncthreads();
+    if (wid == 1) incl += s[0];
+    const uint32_t excl = incl - c;
+    if (pos >= excl && pos < incl && pos - excl < ntiles) {
+        const uint32_t t = o.list[(size_t)tid * ntiles + (pos - excl)];
+        if (t < ntiles) s[1] = t;
+    }
+    __syncthreads();
+    return s[1];
+}
+
 struct RenderArgs {
     const uint2 *ranges;  // by global tile
     const uint32_t *vals;
@@ -126,6 +169,11 @@ struct RenderArgs {
     int blocks_per_sm;   // persistent blocks per SM (0: occupancy limit)
     unsigned long long *counts;  // measurement only (single frame): [evaluated, power test passed] or null
     const CamTile *cam_table;    // persistent launch over ts.n_cams cameras from this device table, or null (ts.cam)
+    // one block per tile (single frame): with order.cnt set, block b renders
+    // the tile at position b of the tiles by decreasing work (TileOrder), else
+    // tile b; with order_out.cnt set, every tile is filed by its largest
+    // last-contributor count (the backward's work)
+    TileOrder order, order_out;
 };
 
 struct BwdArgs {
@@ -144,6 +192,7 @@ struct BwdArgs {
     int tiles_per_fetch;
     int blocks_per_sm;
     const CamTile *cam_table;  // as RenderArgs::cam_table
+    TileOrder order;           // as RenderArgs::order
 };
 
 struct PreBwdArgs {
@@ -194,6 +243,10 @@ cudaError_t launch_tile_count(const uint32_t *keys, uint64_t n_max, const uint64
                               uint32_t *counts, uint2 *ranges, uint32_t *hist, int hist_stride, int digit_bits,
                               int tile_bits, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs &a, int batch, cudaStream_t s);
+// Files every tile of a single frame (a.ts.cam[0]) into a.order by an
+// estimate of the render's work: the entries composited until four sample
+// pixels of the tile stop (the whole list where one does not).
+cudaError_t launch_tile_work(const RenderArgs &a, cudaStream_t s);
 cudaError_t launch_l1_grad(const float *img, const float *target, float *dL, uint64_t n, float scale, double *loss,
                            cudaStream_t s);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, uint64_t n, float lr, float b1, float b2,

@@ -243,6 +243,18 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
             }
         }
     }
+    if (a.order_out.cnt) {
+        // the tile's largest last-contributor count (the backward walks that
+        // many entries) files it for the backward
+        __shared__ int s_last[2];
+        int m = 0;
+#pragma unroll
+        for (int r = 0; r < kRenderPairs; ++r) m = max(m, max(P[r].last0, P[r].last1));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) s_last[wid] = m;
+        __syncthreads();
+        if (tid == 0) order_file(a.order_out, a.ts.total_tiles, gtile, (uint32_t)max(s_last[0], s_last[1]));
+    }
     if (COUNT) {
         unsigned long long ps = npass;
 #pragma unroll
@@ -257,13 +269,118 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
     }
 }
 
-// One block per tile of a single camera.
+// One block per tile of a single camera; with an order, the blocks (which
+// start roughly in index order) take the heaviest tiles first, so that the
+// last blocks to start are short ones.
+static_assert(kRenderThreads == kOrderBuckets, "order_pick reads one bucket per thread");
 template <int BATCH, bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads) render_kernel(RenderArgs a) {
     __shared__ float4 s_stage[5][BATCH];
     __shared__ uint32_t s_mask[2 * BATCH / 32];
     const RenderStage S{s_stage[0], s_stage[1], s_stage[2], s_stage[3], s_stage[4], s_mask};
-    render_tile<BATCH, COUNT>(a, blockIdx.x, a.ts.cam[0], S);
+    __shared__ uint32_t s_pick[2];
+    const uint32_t t =
+        a.order.cnt ? order_pick(a.order, a.ts.total_tiles, blockIdx.x, s_pick) : (uint32_t)blockIdx.x;
+    render_tile<BATCH, COUNT>(a, t, a.ts.cam[0], S);
+}
+
+// A warp per tile walks the tile's list 32 entries at a time for four sample
+// pixels (offsets 3 and 12 in x and y): each lane takes one entry's
+// 1 - alpha at each pixel (the render's accept rules on the plain conic
+// form), a product scan over the lanes gives the transmittance after every
+// entry, and the first entry that takes a pixel below the stop ends that
+// pixel.  The estimate is the largest stop position, or the list length when
+// a pixel has not stopped within kWorkChunks chunks.  The next chunk's
+// records and the one after's indices are loaded while a chunk is scanned.
+constexpr uint32_t kWorkChunks = 32;  // beyond 1024 entries every tile files into the top bucket
+__global__ void __launch_bounds__(256) tile_work_kernel(RenderArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t t = blockIdx.x * 8u + (threadIdx.x >> 5);
+    if (t >= a.ts.total_tiles) return;  // warp-uniform
+    const CamTile &C = a.ts.cam[0];
+    const int tx = (int)(t % (uint32_t)C.tiles_x), ty = (int)(t / (uint32_t)C.tiles_x);
+    float sx[4], sy[4], T[4];
+    bool done[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = tx * kTile + ((k & 1) ? 12 : 3), y = ty * kTile + ((k & 2) ? 12 : 3);
+        sx[k] = (float)x;
+        sy[k] = (float)y;
+        T[k] = 1.f;
+        done[k] = x >= C.W || y >= C.H;
+    }
+    const uint2 range = a.ranges[t];
+    const uint32_t total = range.y - range.x;
+    const uint32_t *vals = a.vals + range.x;
+    // records of chunk 0, indices of chunk 1
+    float2 m = make_float2(0.f, 0.f);
+    float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < total) {
+        const uint32_t g = vals[lane];
+        m = a.xy[g];
+        co = a.conic_o[g];
+    }
+    uint32_t gn = 32 + lane < total ? vals[32 + lane] : 0u;
+    uint32_t work = 0;
+    bool open = true;
+    for (uint32_t c = 0; c < kWorkChunks && 32 * c < total; ++c) {
+        const uint32_t base = 32 * c;
+        const bool have = base + lane < total;
+        const float2 mc = m;
+        const float4 cc = co;
+        if (base + 32 + lane < total) {  // prefetch: records of chunk c + 1, indices of chunk c + 2
+            m = a.xy[gn];
+            co = a.conic_o[gn];
+            gn = base + 64 + lane < total ? vals[base + 64 + lane] : 0u;
+        }
+        float om[4] = {1.f, 1.f, 1.f, 1.f};
+        if (have) {
+            const float skip = skip_threshold(cc.w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float dx = mc.x - sx[k], dy = mc.y - sy[k];
+                const float pw = -0.5f * (cc.x * dx * dx + cc.z * dy * dy) - cc.y * dx * dy;
+                if (pw >= skip) {
+                    const float al = fminf(kAlphaMax, cc.w * __expf(pw));
+                    if (al >= kAlphaMin) om[k] = 1.f - al;
+                }
+            }
+        }
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float v = __shfl_up_sync(0xffffffffu, om[k], o);
+                if (lane >= o) om[k] *= v;
+            }
+            const float Tl = T[k] * om[k];
+            const uint32_t stop = __ballot_sync(0xffffffffu, Tl < kTStop);
+            if (!done[k] && stop) {
+                done[k] = true;
+                work = max(work, base + (uint32_t)__ffs(stop));
+            }
+            T[k] = __shfl_sync(0xffffffffu, Tl, 31);
+            all = all && done[k];
+        }
+        if (all) {
+            open = false;
+            break;
+        }
+    }
+    if (open) {
+        bool any_open = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) any_open = any_open || !done[k];
+        if (any_open) work = total;
+    }
+    if (lane == 0) order_file(a.order, a.ts.total_tiles, t, work);
+}
+
+cudaError_t launch_tile_work(const RenderArgs &a, cudaStream_t s) {
+    if (a.ts.total_tiles == 0) return cudaSuccess;
+    note_launch("tile_work_kernel", s), tile_work_kernel<<<(a.ts.total_tiles + 7) / 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 // Persistent blocks take tiles_per_fetch consecutive tiles at a time from a

@@ -66,6 +66,14 @@ def test_kernel_work_figures():
     w = bench.kernel_work(P, n, (E, Ep))
     assert w["tile_sort_pass"] == ("hbm", 16 * P)
     assert w["tile_sort_pass_values"] == ("hbm", 12 * P)
+    wp = bench.kernel_work(P, n, (E, Ep), packed=True)  # one packed word between the passes
+    assert wp["tile_sort_pass"] == ("hbm", 12 * P)
+    assert wp["tile_sort_pass_values"] == ("hbm", 8 * P)
+    # 1080p: 8160 tiles, 13-bit ids sorted as 7 + 6 bits, indices below 2^26
+    assert bench.tile_sort_packed(1_000_000, 1920, 1080, 8)
+    assert not bench.tile_sort_packed(2 ** 26 + 1, 1920, 1080, 8)
+    assert not bench.tile_sort_packed(1_000, 64, 64, 8)  # 16 tiles: one pass
+    assert not bench.tile_sort_packed(1_000, 16384, 16384, 8)  # 20-bit ids: three passes
     assert w["emit_warp_kernel"] == ("hbm", 8 * P + 28 * n)
     assert w["render_kernel"] == ("alu", 9 * E + 12 * Ep)  # power test on every entry, alpha and blend on passes
     assert w["preprocess_kernel"] == ("hbm", n * bench.PREPROCESS_BYTES)
@@ -96,7 +104,7 @@ def test_roofline_picks_the_dominant_kernel_and_uses_the_measured_peaks():
     assert unit == "eval" and r["traffic"] == int(per * E)
     sp = r["kernels"]["tile_sort_pass"]
     assert sp["bound"] == "hbm" and sp["peak"] == peaks["hbm_gbs"]
-    assert sp["achieved"] == pytest.approx(16 * P / 0.10e-3 / 1e9, rel=1e-3)
+    assert sp["achieved"] == pytest.approx(12 * P / 0.10e-3 / 1e9, rel=1e-3)  # 600k at 1080p: packed
     assert sp["traffic"] == int(bench.TRAFFIC_PER_UNIT["tile_sort_pass"][1] * P)
     assert "not_a_kernel_of_ours" not in r["kernels"]
 
