@@ -734,12 +734,22 @@ __global__ void __launch_bounds__(512) tile_count_kernel(const uint32_t *__restr
     const uint64_t n = device_count(n_dev, n_max);
     const uint64_t n4 = n / 4, stride = (uint64_t)gridDim.x * blockDim.x;
     const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);  // 256-byte aligned buffer
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-        const uint4 v = __ldcs(k4 + i);
-        if (v.x < ntiles) atomicAdd(&s_hist[v.x], 1u);
-        if (v.y < ntiles) atomicAdd(&s_hist[v.y], 1u);
-        if (v.z < ntiles) atomicAdd(&s_hist[v.z], 1u);
-        if (v.w < ntiles) atomicAdd(&s_hist[v.w], 1u);
+    // four independent 16-byte loads in flight per thread
+    constexpr int U = 4;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += U * stride) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t j = i + u * stride;
+            v[u] = j < n4 ? __ldcs(k4 + j) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (v[u].x < ntiles) atomicAdd(&s_hist[v[u].x], 1u);
+            if (v[u].y < ntiles) atomicAdd(&s_hist[v[u].y], 1u);
+            if (v[u].z < ntiles) atomicAdd(&s_hist[v[u].z], 1u);
+            if (v[u].w < ntiles) atomicAdd(&s_hist[v[u].w], 1u);
+        }
     }
     for (uint64_t i = 4 * n4 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t k = keys[i];
