@@ -484,10 +484,11 @@ def kernel_work(P, n, evals, packed=False):
 # captured (kernel -> (unit, bytes per unit)).  A kernel changed since its
 # capture has no entry.
 TRAFFIC_PER_UNIT = {
-    "render_kernel": ("eval", (12.994304e6 + 1.490944e6) / 398728138),
-    "tile_sort_pass": ("pair", (166.163712e6 + 120.412416e6) / 20633099),
-    "tile_sort_pass_values": ("pair", (165.441280e6 + 31.980032e6) / 20633099),
-    "tile_count_kernel": ("pair", (82.601216e6 + 1.472768e6) / 20633099),
+    "render_kernel": ("eval", (13.031680e6 + 0.443648e6) / 398728138),
+    "tile_sort_pass": ("pair", (165.526528e6 + 34.277120e6) / 20633099),
+    "tile_sort_pass_values": ("pair", (82.809600e6 + 35.105536e6) / 20633099),
+    "emit_warp_kernel": ("pair", (52.036864e6 + 118.226176e6) / 20633099),
+    "preprocess_kernel": ("gaussian", (147.195648e6 + 41.842176e6) / 600000),
 }
 
 
@@ -527,7 +528,7 @@ def roofline(fwd_stages, kernels, P, n, W, H, digit_bits, evals, clk, sort_mode,
     for name, r in rows.items():
         if name in TRAFFIC_PER_UNIT:
             unit, per = TRAFFIC_PER_UNIT[name]
-            units = n_eval if unit == "eval" else P
+            units = n_eval if unit == "eval" else (n if unit == "gaussian" else P)
             r["traffic"] = int(per * units) if units else None
     dom = max(rows, key=lambda r: rows[r]["ms_per_step"])
     d = rows[dom]
