@@ -292,6 +292,9 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(RenderArgs a) {
 // pixel.  The estimate is the largest stop position, or the list length when
 // a pixel has not stopped within kWorkChunks chunks.  The next chunk's
 // records and the one after's indices are loaded while a chunk is scanned.
+constexpr int kWorkPix = 4;  // sample pixels per tile, at these offsets in the tile
+__device__ constexpr int kWorkX[kWorkPix] = {3, 12, 3, 12};
+__device__ constexpr int kWorkY[kWorkPix] = {3, 3, 12, 12};
 constexpr uint32_t kWorkChunks = 32;  // beyond 1024 entries every tile files into the top bucket
 __global__ void __launch_bounds__(256) tile_work_kernel(RenderArgs a) {
     const int lane = threadIdx.x & 31;
@@ -299,11 +302,11 @@ __global__ void __launch_bounds__(256) tile_work_kernel(RenderArgs a) {
     if (t >= a.ts.total_tiles) return;  // warp-uniform
     const CamTile &C = a.ts.cam[0];
     const int tx = (int)(t % (uint32_t)C.tiles_x), ty = (int)(t / (uint32_t)C.tiles_x);
-    float sx[4], sy[4], T[4];
-    bool done[4];
+    float sx[kWorkPix], sy[kWorkPix], T[kWorkPix];
+    bool done[kWorkPix];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int x = tx * kTile + ((k & 1) ? 12 : 3), y = ty * kTile + ((k & 2) ? 12 : 3);
+    for (int k = 0; k < kWorkPix; ++k) {
+        const int x = tx * kTile + kWorkX[k], y = ty * kTile + kWorkY[k];
         sx[k] = (float)x;
         sy[k] = (float)y;
         T[k] = 1.f;
@@ -333,11 +336,13 @@ __global__ void __launch_bounds__(256) tile_work_kernel(RenderArgs a) {
             co = a.conic_o[gn];
             gn = base + 64 + lane < total ? vals[base + 64 + lane] : 0u;
         }
-        float om[4] = {1.f, 1.f, 1.f, 1.f};
+        float om[kWorkPix];
+#pragma unroll
+        for (int k = 0; k < kWorkPix; ++k) om[k] = 1.f;
         if (have) {
             const float skip = skip_threshold(cc.w);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < kWorkPix; ++k) {
                 const float dx = mc.x - sx[k], dy = mc.y - sy[k];
                 const float pw = -0.5f * (cc.x * dx * dx + cc.z * dy * dy) - cc.y * dx * dy;
                 if (pw >= skip) {
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(256) tile_work_kernel(RenderArgs a) {
         }
         bool all = true;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kWorkPix; ++k) {
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const float v = __shfl_up_sync(0xffffffffu, om[k], o);
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(256) tile_work_kernel(RenderArgs a) {
     if (open) {
         bool any_open = false;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) any_open = any_open || !done[k];
+        for (int k = 0; k < kWorkPix; ++k) any_open = any_open || !done[k];
         if (any_open) work = total;
     }
     if (lane == 0) order_file(a.order, a.ts.total_tiles, t, work);
