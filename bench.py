@@ -319,6 +319,8 @@ def run_ours(args, rank, world, local_rank):
     n_eval, n_pass = (int(x) for x in cnt.cpu().tolist())
 
     # ---- end to end through the public API with host buffers ----
+    # (as a user calls it: no per-launch timing hook)
+    N.qb_set_launch_hook(None)
     host_img = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in pinned.values())
     d2h = host_img.numel() * 4

@@ -187,6 +187,15 @@ typedef struct {
                                    predecessor unpublished, gives up after k
                                    polls and raises TIMEOUT; the sorted values
                                    are then undefined (do not render them)  */
+    uint32_t *order_counts; /* [2][64] tiles per work bucket, written by the
+                                   forward render: [0] the render's order (by
+                                   an estimate of each tile's work), [1] the
+                                   backward's (by the tile's largest
+                                   n_contrib); bucket j holds work in
+                                   [16 (63 - j), 16 (64 - j)), bucket 0 all
+                                   work from 1008 on                        */
+    uint32_t *order_lists;  /* [2][64][tiles] the tile ids of each bucket,
+                                   the first order_counts[o][j] of row j    */
 } qb_frame_arrays;
 
 /* Thread-local description of the last failure. */

@@ -80,7 +80,8 @@ class QbBatch(ctypes.Structure):
 class QbFrameArrays(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("xy", "conic_o", "rgbd", "box", "r3", "meta", "counts", "offsets",
                                           "keys", "tile_keys", "vals", "depth_order", "ranges", "t_final",
-                                          "n_contrib", "n_eval", "n_pairs", "err_flags")]
+                                          "n_contrib", "n_eval", "n_pairs", "err_flags", "order_counts",
+                                          "order_lists")]
 
 
 _lib = None

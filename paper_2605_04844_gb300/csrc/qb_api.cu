@@ -271,6 +271,8 @@ qb_status qb_frame_arrays_get(const qb_frame *frame, qb_frame_arrays *out) {
     out->n_eval = at<int32_t>(frame, L.neval);
     out->n_pairs = at<uint64_t>(frame, L.state);
     out->err_flags = at<uint32_t>(frame, L.state + 8);
+    out->order_counts = at<uint32_t>(frame, L.order_cnt);
+    out->order_lists = at<uint32_t>(frame, L.order_list);
     return QB_OK;
 }
 

@@ -156,6 +156,8 @@ class Frame:
             "n_contrib": self._view(a.n_contrib, torch.int32, (H, W)),
             "n_eval": self._view(a.n_eval, torch.int32, (H, W)),
             "err_flags": self._view(a.err_flags, torch.int32, (2,)),
+            "order_counts": self._view(a.order_counts, torch.int32, (2, 64)),
+            "order_lists": self._view(a.order_lists, torch.int32, (2, 64, tiles)),
         }
 
 

@@ -254,3 +254,30 @@ def test_counted_render_is_the_same_render_and_counts_its_work():
     # every contributing entry passed the power test; far from all evaluated ones did
     assert n_pass <= n_eval
     assert n_pass >= int((A["n_contrib"] > 0).sum())
+
+
+@pytest.mark.parametrize("maker", [c2_small, lambda: c1_small(n=3000, W=250, H=190)])
+def test_tile_orders_file_every_tile_once_by_its_work(maker):
+    """The render files every tile once into the render's order (by the work
+    estimate) and once into the backward's (64 buckets of 16 entries, heaviest
+    first); the backward's bucket of a tile follows from its pixels' largest
+    n_contrib, exactly."""
+    scene, cam = maker()
+    img, fr, A = run_forward(scene, cam, "quadbox")
+    B = {k: v.cpu().numpy() for k, v in fr.arrays().items()}
+    tiles = fr.frame.tiles_x * fr.frame.tiles_y
+    cnt, lists = B["order_counts"].astype(np.int64), B["order_lists"]
+    for o in range(2):
+        assert int(cnt[o].sum()) == tiles
+        filed = np.concatenate([lists[o, j, :cnt[o, j]] for j in range(64)])
+        np.testing.assert_array_equal(np.sort(filed), np.arange(tiles))
+    H, W = B["n_contrib"].shape
+    tx, ty = fr.frame.tiles_x, fr.frame.tiles_y
+    nc = np.zeros((ty * 16, tx * 16), np.int64)
+    nc[:H, :W] = B["n_contrib"]
+    work = nc.reshape(ty, 16, tx, 16).max(axis=(1, 3)).reshape(-1)
+    want = 63 - np.minimum(work // 16, 63)
+    got = np.empty(tiles, np.int64)
+    for j in range(64):
+        got[lists[1, j, :cnt[1, j]]] = j
+    np.testing.assert_array_equal(got, want)
