@@ -293,16 +293,13 @@ __device__ __forceinline__ void render_bwd_tile(const BwdArgs &a, uint32_t gtile
     }
 }
 
-static_assert(kBwdThreads == kOrderBuckets, "order_pick reads one bucket per thread");
 // One block per tile; with an order, the heaviest tiles first (as the forward).
 __global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(BwdArgs a) {
     __shared__ uint32_t s_id[kBwdBatch];
     __shared__ float4 s_st[6][kBwdBatch];
     __shared__ int s_maxlast;
     const BwdStage S{s_id, s_st[0], s_st[1], s_st[2], s_st[3], s_st[4], s_st[5], &s_maxlast};
-    __shared__ uint32_t s_pick[2];
-    const uint32_t t =
-        a.order.cnt ? order_pick(a.order, a.ts.total_tiles, blockIdx.x, s_pick) : (uint32_t)blockIdx.x;
+    const uint32_t t = a.order.cnt ? order_pick(a.order, a.ts.total_tiles, blockIdx.x) : (uint32_t)blockIdx.x;
     render_bwd_tile(a, t, a.ts.cam[0], S);
 }
 

@@ -127,29 +127,31 @@ __device__ __forceinline__ void order_file(const TileOrder &o, uint32_t ntiles, 
     if (slot < ntiles) o.list[(size_t)j * ntiles + slot] = tile;
 }
 
-// The tile at position pos of the order, for a block of kOrderBuckets threads
-// (thread j reads bucket j); s: three words of shared memory.  Position pos
-// itself when no bucket holds it (never, when every tile was filed once).
-__device__ __forceinline__ uint32_t order_pick(const TileOrder &o, uint32_t ntiles, uint32_t pos, uint32_t *s) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const uint32_t c = o.cnt[tid];
-    uint32_t incl = c;
+// The tile at position pos of the order, found by one warp (every warp of a
+// block finds the same tile, with no shared memory or barrier): lane l reads
+// buckets l and l + 32.  Position pos itself when no bucket holds it (never,
+// when every tile was filed once).
+static_assert(kOrderBuckets == 64, "order_pick reads two buckets per lane");
+__device__ __forceinline__ uint32_t order_pick(const TileOrder &o, uint32_t ntiles, uint32_t pos) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t c0 = o.cnt[lane], c1 = o.cnt[32 + lane];
+    uint32_t i0 = c0, i1 = c1;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += u;
+        const uint32_t u0 = __shfl_up_sync(0xffffffffu, i0, d), u1 = __shfl_up_sync(0xffffffffu, i1, d);
+        if (lane >= d) i0 += u0, i1 += u1;
     }
-    if (tid == 31) s[0] = incl;
-    if (tid == 0) s[1] = pos;
-    __syncthreads();
-    if (wid == 1) incl += s[0];
-    const uint32_t excl = incl - c;
-    if (pos >= excl && pos < incl && pos - excl < ntiles) {
-        const uint32_t t = o.list[(size_t)tid * ntiles + (pos - excl)];
-        if (t < ntiles) s[1] = t;
-    }
-    __syncthreads();
-    return s[1];
+    i1 += __shfl_sync(0xffffffffu, i0, 31);  // inclusive prefixes of buckets lane and 32 + lane
+    const uint32_t e0 = i0 - c0, e1 = i1 - c1;
+    const bool h0 = pos >= e0 && pos < i0 && pos - e0 < ntiles;
+    const bool h1 = pos >= e1 && pos < i1 && pos - e1 < ntiles;
+    uint32_t t = pos;
+    if (h0) t = o.list[(size_t)lane * ntiles + (pos - e0)];
+    if (h1) t = o.list[(size_t)(32 + lane) * ntiles + (pos - e1)];
+    const uint32_t m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+    const int src = m0 ? __ffs(m0) - 1 : (m1 ? __ffs(m1) - 1 : 0);
+    t = __shfl_sync(0xffffffffu, t, src);
+    return (m0 | m1) && t < ntiles ? t : pos;
 }
 
 struct RenderArgs {

@@ -272,15 +272,12 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, uint32_t gtile,
 // One block per tile of a single camera; with an order, the blocks (which
 // start roughly in index order) take the heaviest tiles first, so that the
 // last blocks to start are short ones.
-static_assert(kRenderThreads == kOrderBuckets, "order_pick reads one bucket per thread");
 template <int BATCH, bool COUNT>
 __global__ void __launch_bounds__(kRenderThreads) render_kernel(RenderArgs a) {
     __shared__ float4 s_stage[5][BATCH];
     __shared__ uint32_t s_mask[2 * BATCH / 32];
     const RenderStage S{s_stage[0], s_stage[1], s_stage[2], s_stage[3], s_stage[4], s_mask};
-    __shared__ uint32_t s_pick[2];
-    const uint32_t t =
-        a.order.cnt ? order_pick(a.order, a.ts.total_tiles, blockIdx.x, s_pick) : (uint32_t)blockIdx.x;
+    const uint32_t t = a.order.cnt ? order_pick(a.order, a.ts.total_tiles, blockIdx.x) : (uint32_t)blockIdx.x;
     render_tile<BATCH, COUNT>(a, t, a.ts.cam[0], S);
 }
 
