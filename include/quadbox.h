@@ -279,13 +279,17 @@ qb_status qb_sort(qb_frame *frame, qb_stream_t stream);
 /* Stage 4 (Sec. 2 "Render", Eq. 2): front-to-back compositing per pixel.
  * bg: host float[3] background colour (NULL = black).  d_img: device
  * float [3][height][width] (planar RGB), fully overwritten.  Also writes the
- * frame's t_final and n_contrib, which qb_render_bwd needs. */
+ * frame's t_final and n_contrib, which qb_render_bwd needs.  The tiles run
+ * heaviest first: a first kernel files every tile by an estimate of its work
+ * (order_counts[0] / order_lists[0] of qb_frame_arrays), and the render files
+ * every tile again by its largest n_contrib for qb_render_bwd (the second
+ * order); the image does not depend on the order. */
 qb_status qb_render_fwd(qb_frame *frame, const float *bg, float *d_img, qb_stream_t stream);
 
 /* Measurement only: qb_render_fwd (identical outputs) that also adds, over
  * all pixels, the (pixel, entry) evaluations of Eq. 2's loop up to each
  * pixel's stop to d_counts[0] and those whose exponent passed the power test
- * (power <= 0 and not below the skip threshold, i.e. alpha was computed) to
+ * (not below the skip threshold, i.e. alpha was computed) to
  * d_counts[1].  d_counts: device uint64[2], accumulated (zero them first),
  * 8-byte aligned.  The counted kernel is slower than qb_render_fwd's; the
  * counts give the method's arithmetic work per frame for a roofline. */
@@ -301,7 +305,8 @@ qb_status qb_render_fwd_counted(qb_frame *frame, const float *bg, float *d_img, 
  * double [n][9] = dL/d(mu_x, mu_y, Sigma11, Sigma12, Sigma22, o, r, g, b),
  * Sigma the 2D covariance with Sigma12 counted once (the conic gradient is
  * dL/dLambda = -Sigma dL/dSigma Sigma), and must be zeroed by the caller;
- * the sums over pixels are accumulated in float64. */
+ * the sums over pixels are accumulated in float64.  Tiles run in the order
+ * the last qb_render_fwd of this frame filed (heaviest first). */
 qb_status qb_render_bwd(qb_frame *frame, const qb_scene *scene, const qb_camera *camera, const float *bg,
                         const float *d_dL_dimg, qb_scene_grads *grads, double *d_grad_screen,
                         qb_stream_t stream);
