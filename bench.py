@@ -486,11 +486,12 @@ def kernel_work(P, n, evals, packed=False):
 # captured (kernel -> (unit, bytes per unit)).  A kernel changed since its
 # capture has no entry.
 TRAFFIC_PER_UNIT = {
-    "render_kernel": ("eval", (13.031680e6 + 0.443648e6) / 398728138),
+    "render_kernel": ("eval", (13.032192e6 + 0.436224e6) / 398728138),
     "tile_sort_pass": ("pair", (165.526528e6 + 34.277120e6) / 20633099),
     "tile_sort_pass_values": ("pair", (82.809600e6 + 35.105536e6) / 20633099),
     "emit_warp_kernel": ("pair", (52.036864e6 + 118.226176e6) / 20633099),
     "preprocess_kernel": ("gaussian", (147.195648e6 + 41.842176e6) / 600000),
+    "tile_count_kernel": ("pair", (82.591232e6 + 1.410816e6) / 20633099),
 }
 
 
