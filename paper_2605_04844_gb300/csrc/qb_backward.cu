@@ -2,10 +2,12 @@
 // differentiable rasteriser (Sec. 4.1 states the rasteriser is differentiable;
 // the gradients below differentiate Eq. 2 and the Sec. 2 projection).
 //
-// K7: a 64-thread block per tile (four pixels of a column per thread, rows
-// r, r+4, r+8, r+12, evaluated as two pairs with the packed FP32x2
-// instructions) walks the tile list in reverse, from the largest
-// last-contributor position of its pixels down to 0.  Each pixel recomputes
+// K7: a 64-thread block per tile (each warp a half tile, four pixels of a
+// column per thread, rows r, r+2, r+4, r+6 of the half, evaluated as two
+// pairs with the packed FP32x2 instructions) walks the tile list in reverse,
+// from the largest last-contributor position of its pixels down to 0; the
+// blocks take the tiles by decreasing walk length, the order the forward
+// render filed.  Each pixel recomputes
 // alpha exactly as the forward did and the transmittance by division,
 // T_k = T_{k+1} / (1 - alpha_k); with B_k = sum_{i>k} T_i alpha_i c_i + T_final bg
 // the colour behind entry k,
